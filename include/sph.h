@@ -1,0 +1,199 @@
+/*
+ * sph.h -- C ABI of libsph: FP16 relative-coordinate cell link-list (RCLL)
+ * neighbour search and SPH summation density on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2401.08586 ("A GPU accelerated mixed-precision Smoothed
+ * Particle Hydrodynamics framework with cell-based relative coordinates").
+ * Given N particle positions and a search radius kh (= 2h in the paper), the
+ * library finds, for every particle i, all particles j != i with
+ * |x_i - x_j|^2 < kh^2 (the neighbour definition of the all-list and cell
+ * link-list searches, Section "SPH method", Fig. 3) and can sum the SPH
+ * density rho_i = m W(0, h) + sum_j m W(r_ij / h, h) with the cubic B-spline
+ * W of Eq. 3.
+ *
+ * Precision contract (FP16-RCLL mode): the bulk of the distance tests run in
+ * FP16 on cell-relative coordinates (Eq. 6-7); every pair the FP16 test cannot
+ * reject is re-decided in FP32, and the few pairs inside the FP32 error band
+ * are decided by the FP64 expression (dx0*dx0 + dx1*dx1) + dx2*dx2 < kh*kh on
+ * the caller's coordinates.  The neighbour lists are therefore identical to
+ * an FP64 evaluation of that expression.  Density is accumulated in FP32 in
+ * CSR order.
+ *
+ * Conventions for every entry point:
+ *  - Return value: SPH_OK (0), SPH_PENDING (1, serving only) or a negative
+ *    SPH_ERR_* code.  No C++ exception crosses the ABI.  sph_last_error()
+ *    gives a human-readable message for the calling thread's last failure.
+ *  - "device" pointers are CUDA device memory owned by the caller; "host"
+ *    pointers are ordinary host memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  All device work of a call is enqueued on it; calls
+ *    return without waiting unless the description says they synchronise.
+ *  - Layouts: coordinates are N x dim row-major FP64 (x0 y0 [z0] x1 y1 ...).
+ *    CSR: row_ptr int64[N+1], col int32[nnz].
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SPH_OK 0
+#define SPH_PENDING 1
+#define SPH_ERR_INVALID (-1)      /* bad argument or input (non-finite coordinate, kh <= 0, ...) */
+#define SPH_ERR_CAPACITY (-2)     /* col_capacity < nnz; nothing was written past the end */
+#define SPH_ERR_BUDGET (-3)       /* request exceeds the serving HBM budget */
+#define SPH_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define SPH_ERR_TIMEOUT (-5)      /* a bounded device or host wait ran out */
+#define SPH_ERR_DEVICE_CHECK (-6) /* a device-side consistency check fired */
+#define SPH_ERR_NOMEM (-7)        /* device or host allocation failed */
+#define SPH_ERR_NOT_FOUND (-8)    /* unknown handle or ticket */
+
+/* ---- output row order -------------------------------------------------- */
+/* SPH_ORDER_CELL: rows are the particles in the grid's cell-sorted order
+ *   (row r is input particle orig_id[r], see sph_grid_info) and columns are
+ *   cell-sorted positions, ascending within each row.  This is the order the
+ *   search produces natively.
+ * SPH_ORDER_CANONICAL: rows in input order, columns are input indices,
+ *   ascending within each row (costs an extra permute + per-row sort). */
+#define SPH_ORDER_CELL 0
+#define SPH_ORDER_CANONICAL 1
+
+/* ---- arithmetic of the search ---------------------------------------- */
+/* SPH_PREC_FP16_RCLL: FP16 cell-relative coordinates (Eq. 6), FP16 distance
+ *   test (Eq. 7 with the scale reading h_c/2), FP32 re-decision, FP64 tie tier.
+ * SPH_PREC_FP64_CLL: plain FP64 cell link-list (the paper's high-precision
+ *   approach I, Table 4): FP64 coordinates in cell order, FP64 test, FP64
+ *   density (written out as FP32).  Used as the same-GPU baseline. */
+#define SPH_PREC_FP16_RCLL 0
+#define SPH_PREC_FP64_CLL 1
+
+/* Parameters of one particle system (Eq. 3 and the cell link-list, Fig. 3b). */
+typedef struct sph_params {
+    int32_t dim;        /* 2 or 3 */
+    int32_t order;      /* SPH_ORDER_* of sph_nnps_query / sph_density_sum output */
+    int32_t precision;  /* SPH_PREC_* */
+    int32_t have_box;   /* 1: box_lo/box_hi bound every particle (checked on the
+                           device); 0: the bounding box is computed */
+    double h;           /* smoothing length of W (Eq. 3), > 0 */
+    double kh;          /* search radius, > 0 (the paper uses kh = 2h) */
+    double cell_size;   /* background cell size h_c; 0 selects kh * (1 + 2^-30);
+                           otherwise must be >= kh * (1 + 2^-30) */
+    double box_lo[3];   /* used when have_box == 1 */
+    double box_hi[3];
+    double mass;        /* uniform particle mass m of the density sum */
+} sph_params;
+
+/* Opaque binned particle system.  It owns its device buffers (allocated
+ * stream-ordered on the stream of the call that creates or grows them) and
+ * keeps a reference to the caller's coordinate array, which must stay valid
+ * and unchanged until the grid is re-binned or freed. */
+typedef struct sph_grid_s *sph_grid_t;
+
+typedef struct sph_grid_info {
+    int64_t n;               /* particles binned */
+    int64_t ncell;           /* background cells */
+    int32_t nk[3];           /* cells per axis (nk[2] = 1 in 2D) */
+    int32_t dim;
+    double lo[3];            /* grid origin (box lower corner) */
+    double cell_size;        /* h_c */
+    const int32_t *cell_start; /* device int32[ncell+1]: first sorted position of each cell */
+    const int32_t *orig_id;  /* device int32[n]: sorted position -> input index */
+    const int32_t *rank;     /* device int32[n]: input index -> sorted position */
+    int64_t stat_fp32_pairs; /* pairs re-decided in FP32 by the last query (if counted) */
+    int64_t stat_fp64_pairs; /* pairs decided by the FP64 tier by the last query (if counted) */
+} sph_grid_info;
+
+/*
+ * Bin N particles into background cells and build the search structure
+ * (cell link-list, Section "SPH method" Fig. 3b; normalised cell-relative
+ * coordinates, Eq. 5-6, with the cell centre as reference and unit h_c/2).
+ *   p      host: parameters (copied).
+ *   xyz    device: FP64 coordinates, n x p->dim row-major.  Must stay valid
+ *          and unchanged until *grid is re-binned or freed (the FP64 tier of
+ *          the search reads it).  Must be finite.
+ *   n      number of particles, 0 <= n < 2^31 - 1.
+ *   grid   host: in/out.  If *grid is NULL a new grid is created; otherwise
+ *          the existing grid is re-binned in place (its buffers are reused and
+ *          grown when needed).
+ * Synchronises `stream` once when the bounding box must be computed (to size
+ * the cell array).  Errors: SPH_ERR_INVALID (bad parameters, non-finite
+ * coordinate, more than 2^20 cells per axis or 2^28 cells), SPH_ERR_NOMEM,
+ * SPH_ERR_CUDA.  A particle outside a caller-supplied box is reported by the
+ * next synchronising call as SPH_ERR_INVALID.
+ */
+int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, void *stream,
+                  sph_grid_t *grid);
+
+/*
+ * Neighbour search over a binned grid: emits the CSR neighbour list
+ * (all-list definition, Section "SPH method"; searched over the 3^d cells
+ * around each particle as in the cell link-list, Fig. 3b; pair distance from
+ * cell-relative coordinates as in Eq. 7).  Self is excluded; the test is
+ * strict (r^2 < kh^2).
+ *   row_ptr      device int64[n+1]: written.  row_ptr[n] = nnz.
+ *   col          device int32[col_capacity] or NULL.  NULL: only row_ptr (and
+ *                *nnz_out) are produced.
+ *   col_capacity entries available in col.  If nnz > col_capacity nothing is
+ *                written to col, and the call (or the next synchronising call
+ *                when nnz_out is NULL) returns SPH_ERR_CAPACITY.
+ *   nnz_out      host int64 or NULL.  Non-NULL: the call synchronises `stream`
+ *                and stores nnz.  NULL: the call does not synchronise.
+ *   rho          device float[n] or NULL.  Non-NULL (and col non-NULL): the
+ *                density sum is fused into the search and written in the
+ *                output row order.
+ * Row order follows the grid's sph_params.order.
+ */
+int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity,
+                   int64_t *nnz_out, float *rho, void *stream);
+
+/*
+ * SPH summation density over an existing CSR neighbour list (in the grid's
+ * output order, as produced by sph_nnps_query on this grid):
+ * rho_i = m W(0, h) + sum_{j in N(i)} m W(r_ij / h, h), W from Eq. 3,
+ * accumulated in FP32 in CSR order.
+ *   row_ptr device int64[n+1], col device int32[nnz], rho device float[n].
+ */
+int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, float *rho,
+                    void *stream);
+
+/* Fill *info (host) with the grid's sizes and device pointers.  The pointers
+ * stay valid until the grid is re-binned or freed. */
+int sph_grid_info_get(sph_grid_t grid, sph_grid_info *info);
+
+/* Copy the grid's permutation and cell arrays into caller buffers (device
+ * memory, any may be NULL): orig_id int32[n] (sorted position -> input index),
+ * rank int32[n] (input index -> sorted position), cell_start int32[ncell+1]
+ * (first sorted position of each cell).  Enqueued on `stream`. */
+int sph_grid_export(sph_grid_t grid, int32_t *orig_id, int32_t *rank, int32_t *cell_start,
+                    void *stream);
+
+/* Synchronise `stream` and report any error a device-side check recorded for
+ * this grid since the last synchronising call (SPH_OK if none). */
+int sph_grid_check(sph_grid_t grid, void *stream);
+
+/* Release the grid and its device buffers (stream-ordered on the stream the
+ * grid last used).  NULL is accepted. */
+int sph_grid_free(sph_grid_t grid);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *sph_last_error(void);
+
+/* Error bands of the FP16-RCLL search, in units of u^2 with u = h_c / 2 (the
+ * unit of the normalised relative coordinates of Eq. 6; the threshold is
+ * T = kh^2 / u^2).  A pair is kept by the FP16 test when
+ * r2_fp16 - T < *tau16; a kept pair is a neighbour when r2_fp32 < T - *tau32,
+ * not one when r2_fp32 > T + *tau32, and is decided in FP64 otherwise.
+ * Host pointers; either may be NULL.  No GPU needed. */
+int sph_precision_bands(double *tau16, double *tau32);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

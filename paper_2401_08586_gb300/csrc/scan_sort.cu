@@ -1,0 +1,255 @@
+// scan_sort.cu -- device-wide exclusive scan and segmented sort used by the
+// counting sort of the binning step and by the CSR assembly.
+//
+// Scan: three launches (tile sums, scan of tile sums, tile scan + offset).
+// Sort: every segment is sorted ascending with a bitonic network written so
+// that all comparators put the minimum at the lower index (the first step of
+// each merge compares i with i ^ (k - 1)).  With that form, positions past the
+// segment end behave as +infinity and are simply skipped, so no padding is
+// stored.  Segments of <= 32 keys are sorted in registers by one warp,
+// <= 1024 keys by one warp in shared memory, larger ones by a whole block.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int SCAN_NT = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_NT * SCAN_ITEMS;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan across a 256-thread block; returns the exclusive prefix of
+// v and writes the block total to *total (all threads).
+__device__ long long block_excl_scan_256(long long v, long long *total) {
+    __shared__ long long wsum[SCAN_NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc = warp_incl_scan(v, lane);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < SCAN_NT / 32 ? wsum[lane] : 0;
+        s = warp_incl_scan(s, lane);
+        if (lane < SCAN_NT / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    long long before = w > 0 ? wsum[w - 1] : 0;
+    *total = wsum[SCAN_NT / 32 - 1];
+    __syncthreads();
+    return before + inc - v;
+}
+
+__global__ void __launch_bounds__(SCAN_NT) k_tile_sums(const int *in, long long n, long long *sums) {
+    long long base = (long long)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+#pragma unroll 4
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        long long idx = base + (long long)k * SCAN_NT + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    long long tot;
+    block_excl_scan_256(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: in-place exclusive scan of the tile sums; grand total to sums[ntile].
+__global__ void __launch_bounds__(SCAN_NT) k_scan_sums(long long *sums, long long ntile) {
+    long long carry = 0;
+    for (long long base = 0; base < ntile; base += SCAN_NT) {
+        long long idx = base + threadIdx.x;
+        long long v = idx < ntile ? sums[idx] : 0;
+        long long tot;
+        long long ex = block_excl_scan_256(v, &tot);
+        if (idx < ntile) sums[idx] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) sums[ntile] = carry;
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(SCAN_NT) k_tile_scan(const int *in, OutT *out, long long n,
+                                                        const long long *sums, long long ntile) {
+    __shared__ long long buf[SCAN_TILE];
+    long long base = (long long)blockIdx.x * SCAN_TILE;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        long long idx = base + (long long)k * SCAN_NT + threadIdx.x;
+        buf[k * SCAN_NT + threadIdx.x] = idx < n ? in[idx] : 0;
+    }
+    __syncthreads();
+    long long own[SCAN_ITEMS];
+    long long s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        own[k] = buf[threadIdx.x * SCAN_ITEMS + k];
+        s += own[k];
+    }
+    long long tot;
+    long long ex = block_excl_scan_256(s, &tot) + sums[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        buf[threadIdx.x * SCAN_ITEMS + k] = ex;
+        ex += own[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        long long idx = base + (long long)k * SCAN_NT + threadIdx.x;
+        if (idx < n) out[idx] = (OutT)buf[k * SCAN_NT + threadIdx.x];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (OutT)sums[ntile];
+}
+
+template <typename OutT>
+cudaError_t scan_impl(const int *in, OutT *out, long long n, void *tmp, cudaStream_t s) {
+    long long ntile = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntile == 0) ntile = 1;
+    long long *sums = (long long *)tmp;
+    k_tile_sums<<<(unsigned)ntile, SCAN_NT, 0, s>>>(in, n, sums);
+    k_scan_sums<<<1, SCAN_NT, 0, s>>>(sums, ntile);
+    k_tile_scan<OutT><<<(unsigned)ntile, SCAN_NT, 0, s>>>(in, out, n, sums, ntile);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- sorting
+
+__device__ __forceinline__ int ceil_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// One warp sorts keys[0, len) (len <= 32) held one per lane.
+__device__ __forceinline__ int warp_sort32(int v, int lane, int len) {
+    const int INF = 0x7fffffff;
+    if (lane >= len) v = INF;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            int partner = (j == (k >> 1)) ? (lane ^ (k - 1)) : (lane ^ j);
+            int o = __shfl_sync(0xffffffffu, v, partner);
+            bool lower = lane < partner;
+            v = lower ? min(v, o) : max(v, o);
+        }
+    }
+    return v;
+}
+
+// Compare-exchange network over keys[0, len) in any memory, executed by
+// `nthr` cooperating threads with index `t`; `sync` orders the steps.
+template <typename Sync>
+__device__ void bitonic_all_ascending(int *keys, long long len, int t, int nthr, Sync sync) {
+    long long P = 1;
+    while (P < len) P <<= 1;
+    for (long long k = 2; k <= P; k <<= 1) {
+        for (long long j = k >> 1; j > 0; j >>= 1) {
+            for (long long i = t; i < P; i += nthr) {
+                long long partner = (j == (k >> 1)) ? (i ^ (k - 1)) : (i ^ j);
+                if (partner > i && partner < len) {
+                    int a = keys[i], b = keys[partner];
+                    if (a > b) {
+                        keys[i] = b;
+                        keys[partner] = a;
+                    }
+                }
+            }
+            sync();
+        }
+    }
+}
+
+struct WarpSync {
+    __device__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
+constexpr int SORT_NT = 128;
+constexpr int WARP_SMEM_KEYS = 1024;
+
+template <typename IdxT>
+__global__ void __launch_bounds__(SORT_NT) k_seg_sort_small(int *keys, const IdxT *seg, long long nseg,
+                                                             int *big_list, unsigned int *big_count) {
+    __shared__ int wbuf[SORT_NT / 32][WARP_SMEM_KEYS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long gw = ((long long)blockIdx.x * SORT_NT + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * SORT_NT) >> 5;
+    for (long long c = gw; c < nseg; c += nw) {
+        long long a = seg[c], b = seg[c + 1];
+        long long len = b - a;
+        if (len <= 1) continue;
+        if (len <= 32) {
+            int v = lane < len ? keys[a + lane] : 0;
+            v = warp_sort32(v, lane, (int)len);
+            if (lane < len) keys[a + lane] = v;
+        } else if (len <= WARP_SMEM_KEYS) {
+            int *buf = wbuf[w];
+            for (int i = lane; i < len; i += 32) buf[i] = keys[a + i];
+            __syncwarp();
+            bitonic_all_ascending(buf, len, lane, 32, WarpSync());
+            for (int i = lane; i < len; i += 32) keys[a + i] = buf[i];
+            __syncwarp();
+        } else if (lane == 0) {
+            unsigned int slot = atomicAdd(big_count, 1u);
+            big_list[slot] = (int)c;
+        }
+    }
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(SORT_NT) k_seg_sort_big(int *keys, const IdxT *seg, const int *big_list,
+                                                           const unsigned int *big_count) {
+    unsigned int nbig = *big_count;
+    for (unsigned int b = blockIdx.x; b < nbig; b += gridDim.x) {
+        long long c = big_list[b];
+        long long a = seg[c], len = seg[c + 1] - a;
+        bitonic_all_ascending(keys + a, len, threadIdx.x, SORT_NT, BlockSync());
+    }
+}
+
+template <typename IdxT>
+cudaError_t seg_sort_impl(int *keys, const IdxT *seg, long long nseg, int *big_list,
+                          unsigned int *big_count, cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    cudaMemsetAsync(big_count, 0, sizeof(unsigned int), s);
+    long long blocks = (nseg * 32 + SORT_NT - 1) / SORT_NT;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_seg_sort_small<IdxT><<<(unsigned)blocks, SORT_NT, 0, s>>>(keys, seg, nseg, big_list, big_count);
+    k_seg_sort_big<IdxT><<<152, SORT_NT, 0, s>>>(keys, seg, big_list, big_count);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t scan_tmp_bytes(long long n) {
+    long long ntile = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntile == 0) ntile = 1;
+    return (size_t)(ntile + 1) * sizeof(long long);
+}
+
+cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t s) {
+    return scan_impl<int>(in, out, n, tmp, s);
+}
+
+cudaError_t exclusive_scan_i64(const int *in, long long *out, long long n, void *tmp,
+                               cudaStream_t s) {
+    return scan_impl<long long>(in, out, n, tmp, s);
+}
+
+cudaError_t segmented_sort_i32(int *keys, const int *seg_start, long long nseg, int *big_list,
+                               unsigned int *big_count, cudaStream_t s) {
+    return seg_sort_impl<int>(keys, seg_start, nseg, big_list, big_count, s);
+}
+
+cudaError_t segmented_sort_rows(int *keys, const long long *row_ptr, long long nrows,
+                                int *big_list, unsigned int *big_count, cudaStream_t s) {
+    return seg_sort_impl<long long>(keys, row_ptr, nrows, big_list, big_count, s);
+}
+
+}  // namespace sph

@@ -1,0 +1,110 @@
+// sph_internal.cuh -- device-side structures shared by the libsph kernels.
+//
+// Notation (arXiv 2401.08586): h is the smoothing length, kh the search
+// radius, h_c the background cell size, u = h_c / 2 the unit of the
+// normalised cell-relative coordinates of Eq. 6 (x_rel = 2 (x - x_cc) / h_c,
+// in [-1, 1], x_cc the cell centre).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph.h"
+
+namespace sph {
+
+// Bits of the per-grid device status word.
+enum : unsigned int {
+    ST_NONFINITE = 1u << 0,     // a coordinate was NaN or infinite
+    ST_OUT_OF_BOX = 1u << 1,    // a particle lies outside the caller's box
+    ST_TIMEOUT = 1u << 2,       // a bounded device wait ran out
+    ST_CAPACITY = 1u << 3,      // nnz exceeded the col capacity
+    ST_DEVICE_CHECK = 1u << 4,  // an internal consistency check fired
+};
+
+// Small device-resident record each grid owns: status flags, bounding-box
+// reduction slots (doubles mapped to order-preserving unsigned keys) and
+// counters of the precision tiers.
+struct DevStatus {
+    unsigned int flags;
+    unsigned int big_cells;          // cells with more than 32 particles (sort fallback list length)
+    unsigned long long min_key[3];
+    unsigned long long max_key[3];
+    unsigned long long fp32_pairs;   // pairs re-decided in FP32
+    unsigned long long fp64_pairs;   // pairs decided by the FP64 tier
+    long long nnz;
+    unsigned long long ticket;       // tile ticket of the single-pass query
+};
+
+// Everything a search kernel needs, passed by value.
+struct GridDev {
+    int dim;
+    int n;
+    int nk[3];
+    long long ncell;
+    double lo[3];
+    double hc;           // h_c
+    double two_over_hc;  // 2 / h_c: FP64 units -> u
+    const int *cell_start;
+    const uint2 *rel16;   // per sorted particle: half x_rel, y_rel | z_rel, 0
+    const float4 *rel32;  // per sorted particle: x_rel, y_rel, z_rel, 0
+    const double *x64;    // FP64-CLL mode: cell-ordered coordinates, 4 doubles per particle
+    const int *orig_id;   // sorted position -> input index
+    const double *xyz;    // caller coordinates (input order, n x dim)
+    double kh2;           // kh * kh in FP64 (the oracle's threshold)
+    float t32_in;         // FP32 tier: r2_u < t32_in  -> neighbour
+    float t32_out;        // FP32 tier: r2_u > t32_out -> not a neighbour; between -> FP64 tier
+    unsigned int neg_t16; // half2 bits of (-T, -T), T = kh^2 / u^2 rounded to FP16
+    unsigned int tau16;   // half2 bits of the FP16 "maybe" bound
+    float r_scale;        // u / h: R = sqrt(r2_u) * r_scale
+    float w_norm;         // m * alpha_d
+    float w_self;         // m * W(0, h)
+    double r_scale64;     // FP64-CLL mode: 1 / h
+    double w_norm64;      // FP64-CLL mode: m * alpha_d
+    double w_self64;
+    DevStatus *status;
+};
+
+// Order-preserving map from a finite double to an unsigned 64-bit key.
+__host__ __device__ inline unsigned long long dkey(double x) {
+    unsigned long long b;
+    memcpy(&b, &x, 8);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double dkey_inv(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+}
+
+// Cell coordinate along one axis: clamp(floor((x - lo) / h_c), 0, nk - 1),
+// evaluated in FP64 exactly as written (IEEE division, no contraction).
+__device__ __forceinline__ int cell_coord(double x, double lo, double hc, int nk) {
+    double t = floor(__ddiv_rn(__dsub_rn(x, lo), hc));
+    t = fmax(t, 0.0);
+    t = fmin(t, (double)(nk - 1));
+    return (int)t;
+}
+
+// ---- launch helpers (implemented in scan.cu / sort.cu) --------------------
+
+// Exclusive scan of int32 counts into int32 (cell starts) or int64 (row
+// pointers) with the grand total written at out[n].  tmp needs
+// scan_tmp_bytes(n) bytes.
+size_t scan_tmp_bytes(long long n);
+cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t s);
+cudaError_t exclusive_scan_i64(const int *in, long long *out, long long n, void *tmp,
+                               cudaStream_t s);
+
+// Sort every segment [seg_start[c], seg_start[c+1]) of keys ascending, for
+// c < nseg.  Segments longer than 32 are listed in big_list (capacity nseg)
+// with their count in *big_count (device) and sorted by a block-level pass.
+cudaError_t segmented_sort_i32(int *keys, const int *seg_start, long long nseg, int *big_list,
+                               unsigned int *big_count, cudaStream_t s);
+// Same for int64-delimited segments (CSR rows).
+cudaError_t segmented_sort_rows(int *keys, const long long *row_ptr, long long nrows,
+                                int *big_list, unsigned int *big_count, cudaStream_t s);
+
+}  // namespace sph

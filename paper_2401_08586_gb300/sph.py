@@ -1,0 +1,293 @@
+"""ctypes binding of libsph (include/sph.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under the same name and takes the
+same arguments; torch tensors are accepted wherever the C call takes a device
+pointer (their ``data_ptr()`` is passed) and streams default to torch's current
+stream.  All the computation happens in the CUDA library; if ``libsph.so`` is
+missing or no GPU is present the calls raise instead of falling back.
+
+Convenience wrappers (:class:`Grid`, :func:`neighbours`) only allocate the torch
+output tensors and sequence the C calls.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPH_OK = 0
+SPH_PENDING = 1
+SPH_ERR_INVALID = -1
+SPH_ERR_CAPACITY = -2
+SPH_ERR_BUDGET = -3
+SPH_ERR_CUDA = -4
+SPH_ERR_TIMEOUT = -5
+SPH_ERR_DEVICE_CHECK = -6
+SPH_ERR_NOMEM = -7
+SPH_ERR_NOT_FOUND = -8
+
+SPH_ORDER_CELL = 0
+SPH_ORDER_CANONICAL = 1
+SPH_PREC_FP16_RCLL = 0
+SPH_PREC_FP64_CLL = 1
+
+_ERRNAMES = {v: k for k, v in dict(globals()).items() if k.startswith("SPH_ERR_") or k in ("SPH_OK", "SPH_PENDING")}
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "SPH_ERR"), code, msg))
+        self.code = code
+
+
+class sph_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("order", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("have_box", ctypes.c_int32), ("h", ctypes.c_double), ("kh", ctypes.c_double),
+                ("cell_size", ctypes.c_double), ("box_lo", ctypes.c_double * 3),
+                ("box_hi", ctypes.c_double * 3), ("mass", ctypes.c_double)]
+
+
+class sph_grid_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ncell", ctypes.c_int64), ("nk", ctypes.c_int32 * 3),
+                ("dim", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("cell_size", ctypes.c_double),
+                ("cell_start", ctypes.c_void_p), ("orig_id", ctypes.c_void_p), ("rank", ctypes.c_void_p),
+                ("stat_fp32_pairs", ctypes.c_int64), ("stat_fp64_pairs", ctypes.c_int64)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libsph.so (building it first if asked).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libsph.so is not built (%s); run __graft_entry__.build()" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    sig = {
+        "sph_bin_cells": [ctypes.POINTER(sph_params), _vp, ctypes.c_int64, _vp, ctypes.POINTER(_vp)],
+        "sph_nnps_query": [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp, _vp],
+        "sph_density_sum": [_vp, _vp, _vp, _vp, _vp],
+        "sph_grid_info_get": [_vp, ctypes.POINTER(sph_grid_info)],
+        "sph_grid_export": [_vp, _vp, _vp, _vp, _vp],
+        "sph_grid_check": [_vp, _vp],
+        "sph_grid_free": [_vp],
+        "sph_last_error": [],
+        "sph_precision_bands": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "sph_version": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "sph_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C-ABI entry points this binding expects."""
+    return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
+            "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
+            "sph_precision_bands", "sph_version"]
+
+
+def _check(rc):
+    if rc < 0:
+        raise SphError(rc, load().sph_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- the C entry points, same names ----------------------------------------
+
+def sph_bin_cells(params, xyz, n, stream=None, grid=None):
+    """Returns the (possibly new) grid handle (an int)."""
+    g = _vp(grid)
+    _check(load().sph_bin_cells(ctypes.byref(params), _ptr(xyz), int(n), _stream(stream), ctypes.byref(g)))
+    return g.value
+
+
+def sph_nnps_query(grid, row_ptr, col=None, col_capacity=0, want_nnz=True, rho=None, stream=None):
+    """Returns nnz (an int) when want_nnz, else None."""
+    nnz = ctypes.c_int64(-1)
+    _check(load().sph_nnps_query(grid, _ptr(row_ptr), _ptr(col), int(col_capacity),
+                                 ctypes.byref(nnz) if want_nnz else None, _ptr(rho), _stream(stream)))
+    return nnz.value if want_nnz else None
+
+
+def sph_density_sum(grid, row_ptr, col, rho, stream=None):
+    _check(load().sph_density_sum(grid, _ptr(row_ptr), _ptr(col), _ptr(rho), _stream(stream)))
+
+
+def sph_grid_info_get(grid):
+    info = sph_grid_info()
+    _check(load().sph_grid_info_get(grid, ctypes.byref(info)))
+    return info
+
+
+def sph_grid_export(grid, orig_id=None, rank=None, cell_start=None, stream=None):
+    _check(load().sph_grid_export(grid, _ptr(orig_id), _ptr(rank), _ptr(cell_start), _stream(stream)))
+
+
+def sph_grid_check(grid, stream=None):
+    return _check(load().sph_grid_check(grid, _stream(stream)))
+
+
+def sph_grid_free(grid):
+    if grid:
+        _check(load().sph_grid_free(grid))
+
+
+def sph_last_error():
+    return load().sph_last_error().decode()
+
+
+def sph_precision_bands():
+    """(tau16, tau32) of the FP16 test and FP32 re-decision, in units of u^2."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().sph_precision_bands(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def sph_version():
+    return load().sph_version()
+
+
+# ---- convenience ------------------------------------------------------------
+
+def make_params(dim, h, kh=None, order=SPH_ORDER_CELL, precision=SPH_PREC_FP16_RCLL, mass=1.0,
+                cell_size=0.0, box=None):
+    p = sph_params()
+    p.dim = int(dim)
+    p.order = int(order)
+    p.precision = int(precision)
+    p.h = float(h)
+    p.kh = float(2.0 * h if kh is None else kh)
+    p.cell_size = float(cell_size)
+    p.mass = float(mass)
+    if box is not None:
+        p.have_box = 1
+        lo, hi = box
+        for k in range(dim):
+            p.box_lo[k] = float(lo[k])
+            p.box_hi[k] = float(hi[k])
+    return p
+
+
+class Grid:
+    """A binned particle system on the current CUDA device.
+
+    ``xyz`` is an (N, dim) float64 CUDA tensor; it is referenced (not copied),
+    so it is kept alive here.
+    """
+
+    def __init__(self, xyz, h, kh=None, order=SPH_ORDER_CELL, precision=SPH_PREC_FP16_RCLL, mass=1.0,
+                 cell_size=0.0, box=None, stream=None):
+        import torch
+        if not (isinstance(xyz, torch.Tensor) and xyz.is_cuda and xyz.dtype == torch.float64):
+            raise TypeError("xyz must be a float64 CUDA tensor")
+        self.xyz = xyz.contiguous()
+        self.params = make_params(self.xyz.shape[1], h, kh, order, precision, mass, cell_size, box)
+        self.handle = None
+        self.handle = sph_bin_cells(self.params, self.xyz, self.xyz.shape[0], stream, None)
+
+    def rebin(self, xyz=None, stream=None):
+        if xyz is not None:
+            self.xyz = xyz.contiguous()
+        sph_bin_cells(self.params, self.xyz, self.xyz.shape[0], stream, self.handle)
+
+    @property
+    def n(self):
+        return self.xyz.shape[0]
+
+    def info(self):
+        return sph_grid_info_get(self.handle)
+
+    def orig_id(self, stream=None):
+        """int32[N] tensor: sorted position -> input index."""
+        import torch
+        out = torch.empty(self.n, dtype=torch.int32, device=self.xyz.device)
+        sph_grid_export(self.handle, out, None, None, stream)
+        return out
+
+    def rank(self, stream=None):
+        """int32[N] tensor: input index -> sorted position."""
+        import torch
+        out = torch.empty(self.n, dtype=torch.int32, device=self.xyz.device)
+        sph_grid_export(self.handle, None, out, None, stream)
+        return out
+
+    def cell_start(self, stream=None):
+        import torch
+        out = torch.empty(int(self.info().ncell) + 1, dtype=torch.int32, device=self.xyz.device)
+        sph_grid_export(self.handle, None, None, out, stream)
+        return out
+
+    def query(self, density=True, col_capacity=None, stream=None):
+        """Run the search; returns (row_ptr int64[N+1], col int32[nnz], rho float32[N] or None)."""
+        import torch
+        dev = self.xyz.device
+        row_ptr = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        if col_capacity is None:
+            nnz = sph_nnps_query(self.handle, row_ptr, None, 0, True, None, stream)
+            col_capacity = nnz
+        col = torch.empty(max(int(col_capacity), 1), dtype=torch.int32, device=dev)
+        rho = torch.empty(self.n, dtype=torch.float32, device=dev) if density else None
+        nnz = sph_nnps_query(self.handle, row_ptr, col, col.numel(), True, rho, stream)
+        return row_ptr, col[:nnz], rho
+
+    def density(self, row_ptr, col, stream=None):
+        import torch
+        rho = torch.empty(self.n, dtype=torch.float32, device=self.xyz.device)
+        sph_density_sum(self.handle, row_ptr, col, rho, stream)
+        return rho
+
+    def check(self, stream=None):
+        return sph_grid_check(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            sph_grid_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def neighbours(xyz, h, kh=None, order=SPH_ORDER_CANONICAL, precision=SPH_PREC_FP16_RCLL, density=True,
+               mass=1.0):
+    """One-shot search on a CUDA float64 tensor: returns (row_ptr, col, rho)."""
+    g = Grid(xyz, h, kh, order, precision, mass)
+    try:
+        return g.query(density=density)
+    finally:
+        g.close()

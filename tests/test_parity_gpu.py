@@ -1,0 +1,210 @@
+"""Parity of the CUDA path with the FP64 oracle (GPU required).
+
+Neighbour lists must be identical (bit-exact integer CSR); densities within
+1e-5 relative of the FP64 oracle (the FP32-accumulation tolerance of the
+path).  Every call goes through the C ABI (paper_2401_08586_gb300.sph).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_08586_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RHO_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sph():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_08586_gb300 import sph as _sph
+    _sph.load()
+    return _sph
+
+
+def run(sph, xyz, h, kh, order, precision=0, density=True, mass=1.0, box=None, cell_size=0.0):
+    x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float64)).cuda()
+    g = sph.Grid(x, h, kh, order=order, precision=precision, mass=mass, box=box, cell_size=cell_size)
+    rp, col, rho = g.query(density=density)
+    torch.cuda.synchronize()
+    out = dict(rp=rp.cpu().numpy(), col=col.cpu().numpy(), rho=None if rho is None else rho.cpu().numpy(),
+               orig=g.orig_id().cpu().numpy(), rank=g.rank().cpu().numpy(), info=g.info(), grid=g, x=x)
+    return out
+
+
+def to_canonical(rp, col, orig):
+    """CELL-order CSR (rows/cols are sorted positions) -> input-order CSR."""
+    n = rp.size - 1
+    lens = np.diff(rp)
+    rows_in = orig  # row r is input particle orig[r]
+    new_len = np.empty(n, dtype=np.int64)
+    new_len[rows_in] = lens
+    new_rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(new_len, out=new_rp[1:])
+    new_col = np.empty_like(col)
+    for r in range(n):
+        seg = np.sort(orig[col[rp[r]:rp[r + 1]]])
+        i = rows_in[r]
+        new_col[new_rp[i]:new_rp[i + 1]] = seg
+    return new_rp, new_col
+
+
+def check_against_oracle(out, xyz, h, kh, order, mass=1.0, density=True):
+    rp_ref, col_ref = oracle.cll(xyz, kh)
+    rp, col = out["rp"], out["col"]
+    if order == 0:
+        # columns ascending within each row in cell order
+        for r in range(min(rp.size - 1, 2000)):
+            assert np.all(np.diff(col[rp[r]:rp[r + 1]]) > 0)
+        rp, col = to_canonical(rp, col, out["orig"])
+    assert np.array_equal(rp, rp_ref), "row_ptr differs"
+    assert np.array_equal(col, col_ref), "col differs"
+    if density:
+        rho_ref = oracle.density(xyz, h, rp_ref, col_ref, mass=mass)
+        rho = out["rho"].astype(np.float64)
+        if order == 0:
+            r2 = np.empty_like(rho)
+            r2[out["orig"]] = rho
+            rho = r2
+        rel = np.abs(rho - rho_ref) / np.abs(rho_ref)
+        assert rel.max() <= RHO_RTOL, rel.max()
+        return rel.max()
+    return None
+
+
+CASES = {
+    "c1_2d_10k": lambda: (W.c1_2d_10k().xyz, W.c1_2d_10k().h),
+    "lattice3d_27k": lambda: (W.c2_3d_1m(side=30).xyz, 0.013),
+    "random2d": lambda: (W.random_uniform(5000, 2, 3), 0.006),
+    "random3d": lambda: (W.random_uniform(6000, 3, 4), 0.03),
+    "faces3d": lambda: (W.face_set(0.1, 3, 7), 0.05),
+    "faces2d": lambda: (W.face_set(0.1, 2, 8), 0.05),
+    "circle2d_1e-8": lambda: (W.circle_pairs(0.05, 1e-8, 2000, 2, 9), 0.025),
+    "circle3d_1e-12": lambda: (W.circle_pairs(0.05, 1e-12, 2000, 3, 10), 0.025),
+    "circle3d_1e-3": lambda: (W.circle_pairs(0.05, 1e-3, 2000, 3, 11), 0.025),
+    "dambreak_small": lambda: (W.c3_3d_dambreak(side=24).xyz, W.c3_3d_dambreak(side=24).h),
+    "one": lambda: (np.array([[0.3, 0.3, 0.3]]), 0.01),
+    "two": lambda: (np.array([[0.0, 0.0], [0.01, 0.0]]), 0.01),
+    "line": lambda: (np.stack([np.linspace(0, 1, 3000), np.zeros(3000), np.zeros(3000)], 1), 0.0005),
+}
+
+
+@pytest.mark.parametrize("order", [0, 1], ids=["cell", "canonical"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_parity_fp16_rcll(sph, case, order):
+    xyz, h = CASES[case]()
+    out = run(sph, xyz, h, 2 * h, order)
+    check_against_oracle(out, xyz, h, 2 * h, order)
+    assert sph.sph_grid_check(out["grid"].handle) == 0
+
+
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "faces3d", "circle3d_1e-12", "dambreak_small"])
+def test_parity_fp64_cll(sph, case):
+    xyz, h = CASES[case]()
+    out = run(sph, xyz, h, 2 * h, 1, precision=sph.SPH_PREC_FP64_CLL)
+    check_against_oracle(out, xyz, h, 2 * h, 1)
+
+
+def test_exact_ties_power_of_two_lattice(sph):
+    """dx = 1/256 and kh = 3 dx: 30 exact ties per interior particle, all
+    excluded by the strict test; they reach the FP64 tier."""
+    dx = 1.0 / 256
+    xyz = W.exact_lattice(14, 3, dx)
+    out = run(sph, xyz, 1.5 * dx, 3 * dx, 1)
+    check_against_oracle(out, xyz, 1.5 * dx, 3 * dx, 1)
+    assert out["grid"].info().stat_fp64_pairs > 0
+
+
+def test_coincident_and_crowded_cells(sph):
+    """Cells with more than 32 particles (several home batches) and more than
+    1024 candidates (several candidate windows)."""
+    rng = np.random.default_rng(5)
+    xyz = np.vstack([np.full((70, 3), 0.5), rng.uniform(0.45, 0.55, size=(1500, 3)),
+                     rng.uniform(0, 1, size=(500, 3))])
+    out = run(sph, xyz, 0.02, 0.04, 1)
+    check_against_oracle(out, xyz, 0.02, 0.04, 1)
+
+
+def test_empty_input(sph):
+    x = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    g = sph.Grid(x, 0.01)
+    rp, col, rho = g.query()
+    assert rp.cpu().tolist() == [0] and col.numel() == 0
+
+
+def test_mass_and_cell_size(sph):
+    ps = W.c1_2d_10k(side=50)
+    out = run(sph, ps.xyz, ps.h, ps.kh, 1, mass=2.5, cell_size=ps.kh * 1.7)
+    check_against_oracle(out, ps.xyz, ps.h, ps.kh, 1, mass=2.5)
+
+
+def test_user_box(sph):
+    ps = W.c2_3d_1m(side=16)
+    out = run(sph, ps.xyz, ps.h, ps.kh, 1, box=((-0.01, -0.01, -0.01), (0.2, 0.2, 0.2)))
+    check_against_oracle(out, ps.xyz, ps.h, ps.kh, 1)
+    # a particle outside the box is reported
+    bad = ps.xyz.copy()
+    bad[0, 0] = 0.5
+    x = torch.from_numpy(bad).cuda()
+    with pytest.raises(sph.SphError) as ei:
+        g = sph.Grid(x, ps.h, ps.kh, box=((-0.01,) * 3, (0.2,) * 3))
+        g.query()
+    assert ei.value.code == sph.SPH_ERR_INVALID
+
+
+def test_nonfinite_rejected(sph):
+    xyz = W.random_uniform(100, 3, 1)
+    xyz[7, 1] = np.nan
+    with pytest.raises(sph.SphError) as ei:
+        sph.Grid(torch.from_numpy(xyz).cuda(), 0.05)
+    assert ei.value.code == sph.SPH_ERR_INVALID
+
+
+def test_capacity_error_writes_nothing(sph):
+    ps = W.c1_2d_10k(side=30)
+    x = torch.from_numpy(ps.xyz).cuda()
+    g = sph.Grid(x, ps.h, ps.kh)
+    rp = torch.empty(ps.n + 1, dtype=torch.int64, device="cuda")
+    nnz = sph.sph_nnps_query(g.handle, rp, None, 0)
+    cap = nnz - 10
+    buf = torch.full((nnz + 100,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(sph.SphError) as ei:
+        sph.sph_nnps_query(g.handle, rp, buf, cap)
+    assert ei.value.code == sph.SPH_ERR_CAPACITY
+    assert torch.all(buf == -7)
+
+
+def test_unfused_density_matches(sph):
+    for order in (0, 1):
+        ps = W.c2_3d_1m(side=20)
+        out = run(sph, ps.xyz, ps.h, ps.kh, order)
+        g = out["grid"]
+        rp = torch.from_numpy(out["rp"]).cuda()
+        col = torch.from_numpy(out["col"]).cuda()
+        rho2 = g.density(rp, col).cpu().numpy()
+        rel = np.abs(rho2.astype(np.float64) - out["rho"]) / out["rho"]
+        assert rel.max() <= 2e-6
+
+
+def test_rebin_in_place(sph):
+    a = W.c2_3d_1m(side=12)
+    b = W.c2_3d_1m(side=18, seed=9)
+    x = torch.from_numpy(a.xyz).cuda()
+    g = sph.Grid(x, a.h, a.kh, order=1)
+    g.query()
+    g.rebin(torch.from_numpy(b.xyz).cuda())
+    rp, col, rho = g.query()
+    rp_ref, col_ref = oracle.cll(b.xyz, b.kh)
+    assert np.array_equal(rp.cpu().numpy(), rp_ref) and np.array_equal(col.cpu().numpy(), col_ref)
+
+
+def test_deterministic(sph):
+    ps = W.c2_3d_1m(side=24)
+    a = run(sph, ps.xyz, ps.h, ps.kh, 0)
+    b = run(sph, ps.xyz, ps.h, ps.kh, 0)
+    assert np.array_equal(a["rp"], b["rp"]) and np.array_equal(a["col"], b["col"])
+    assert np.array_equal(a["rho"], b["rho"])
+    assert np.array_equal(a["orig"], b["orig"])
