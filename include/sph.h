@@ -182,6 +182,37 @@ int sph_grid_free(sph_grid_t grid);
 /* Message for the calling thread's last failed call ("" if none). */
 const char *sph_last_error(void);
 
+/*
+ * One call from host memory: copy xyz (host, n x p->dim FP64, preferably
+ * pinned) into a device buffer owned by the grid, bin it (as
+ * sph_bin_cells), search with the fused density (as sph_nnps_query), copy
+ * the density (host float[n], may be NULL; in the grid's output row order)
+ * and nnz (host, may be NULL) back.  The CSR stays on the device in
+ * grid-owned buffers (sph_grid_csr); the grid grows them as needed.
+ * *grid as in sph_bin_cells.  Synchronises `stream`.  Errors as
+ * sph_bin_cells and sph_nnps_query.
+ */
+int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, float *rho_host,
+                    int64_t *nnz_host, sph_grid_t *grid, void *stream);
+
+/* Device pointers of the grid-owned CSR and density written by the last
+ * sph_search_host on this grid (host out-pointers; any may be NULL). */
+int sph_grid_csr(sph_grid_t grid, const int64_t **row_ptr, const int32_t **col, const float **rho,
+                 int64_t *nnz);
+
+/* Per-kernel device timing of the library's own launches.  While enabled,
+ * every launch is bracketed by CUDA events recorded on its stream.
+ * sph_profile_read waits for the recorded events and returns the summed
+ * milliseconds and launch count for one kernel tag since the last reset:
+ * "bounds", "hash", "scan", "scatter", "sort", "convert", "count", "fill",
+ * "density", "canon". */
+int sph_profile_enable(int on);
+int sph_profile_reset(void);
+int sph_profile_read(const char *kernel, double *total_ms, int64_t *launches);
+
+/* Number of kernels the library has launched since it was loaded. */
+int64_t sph_launch_count(void);
+
 /* Error bands of the FP16-RCLL search, in units of u^2 with u = h_c / 2 (the
  * unit of the normalised relative coordinates of Eq. 6; the threshold is
  * T = kh^2 / u^2).  A pair is kept by the FP16 test when

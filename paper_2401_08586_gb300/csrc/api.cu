@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 
+#include "profile.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -79,7 +80,8 @@ struct sph_grid_s {
     double hc = 0;
     const double *xyz = nullptr;
     DevBuf cell_start, cnt, cid, slot, orig_id, rank, scell, rel16, rel32, x64, scan_tmp, big_list,
-        rowcnt, tmp_rp, tmp_col, tmp_rho, status;
+        rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho;
+    long long own_nnz = 0;
     DevStatus *h_status = nullptr;  // pinned host mirror
 };
 
@@ -292,6 +294,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
     int rc = SPH_OK;
     do {
         if ((rc = ensure(g->status, sizeof(DevStatus), s)) != SPH_OK) break;
+        note_launch(1);
         k_status_init<<<1, 1, 0, s>>>(P<DevStatus>(g->status));
         double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
         if (p->have_box) {
@@ -393,6 +396,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         return SPH_OK;
     }
     GridDev d = make_dev(g);
+    note_launch(1);
     k_status_reset_counters<<<1, 1, 0, s>>>(P<DevStatus>(g->status));
     SPH_TRY(ensure(g->rowcnt, n * sizeof(int), s));
     const bool canonical = g->p.order == SPH_ORDER_CANONICAL;
@@ -514,13 +518,77 @@ extern "C" int sph_grid_check(sph_grid_t grid, void *stream) {
     return status_to_code(g->h_status->flags);
 }
 
+extern "C" int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, float *rho_host,
+                               int64_t *nnz_host, sph_grid_t *grid, void *stream) {
+    if (!grid) return fail(SPH_ERR_INVALID, "grid is NULL");
+    SPH_TRY(validate(p, n, xyz_host));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (*grid == nullptr) SPH_TRY(grid_create(grid));
+    sph_grid_s *g = *grid;
+    g->stream = s;
+    const size_t xbytes = (size_t)(n > 0 ? n : 1) * p->dim * sizeof(double);
+    SPH_TRY(ensure(g->own_xyz, xbytes, s));
+    if (n > 0) SPH_CUDA(cudaMemcpyAsync(g->own_xyz.p, xyz_host, (size_t)n * p->dim * sizeof(double),
+                                        cudaMemcpyHostToDevice, s));
+    SPH_TRY(sph_bin_cells(p, P<double>(g->own_xyz), n, stream, grid));
+    SPH_TRY(ensure(g->own_rp, (size_t)(n + 1) * sizeof(long long), s));
+    SPH_TRY(ensure(g->own_rho, (size_t)(n > 0 ? n : 1) * sizeof(float), s));
+    int64_t nnz = 0;
+    const long long cap = (long long)(g->own_col.cap / sizeof(int));
+    int rc = sph_nnps_query(g, P<int64_t>(g->own_rp), g->own_col.p ? P<int32_t>(g->own_col) : nullptr, cap,
+                            &nnz, g->own_col.p ? P<float>(g->own_rho) : nullptr, stream);
+    if (rc == SPH_ERR_CAPACITY || (rc == SPH_OK && !g->own_col.p)) {
+        SPH_TRY(ensure(g->own_col, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int), s));
+        rc = sph_nnps_query(g, P<int64_t>(g->own_rp), P<int32_t>(g->own_col),
+                            (long long)(g->own_col.cap / sizeof(int)), &nnz, P<float>(g->own_rho), stream);
+    }
+    if (rc != SPH_OK) return rc;
+    g->own_nnz = nnz;
+    if (rho_host && n > 0)
+        SPH_CUDA(cudaMemcpyAsync(rho_host, g->own_rho.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    if (nnz_host) *nnz_host = nnz;
+    return SPH_OK;
+}
+
+extern "C" int sph_grid_csr(sph_grid_t grid, const int64_t **row_ptr, const int32_t **col, const float **rho,
+                            int64_t *nnz) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (row_ptr) *row_ptr = P<int64_t>(g->own_rp);
+    if (col) *col = P<int32_t>(g->own_col);
+    if (rho) *rho = P<float>(g->own_rho);
+    if (nnz) *nnz = g->own_nnz;
+    return SPH_OK;
+}
+
+extern "C" int sph_profile_enable(int on) {
+    prof_enable(on);
+    return SPH_OK;
+}
+
+extern "C" int sph_profile_reset(void) {
+    prof_reset();
+    return SPH_OK;
+}
+
+extern "C" int sph_profile_read(const char *kernel, double *total_ms, int64_t *launches) {
+    if (!kernel) return fail(SPH_ERR_INVALID, "kernel name is NULL");
+    long long c = 0;
+    if (prof_read(kernel, total_ms, &c) != 0) return fail(SPH_ERR_NOT_FOUND, "unknown kernel tag %s", kernel);
+    if (launches) *launches = c;
+    return SPH_OK;
+}
+
+extern "C" int64_t sph_launch_count(void) { return launch_count(); }
+
 extern "C" int sph_grid_free(sph_grid_t grid) {
     sph_grid_s *g = grid;
     if (!g) return SPH_OK;
     cudaStream_t s = g->stream;
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
                       &g->rel16, &g->rel32, &g->x64, &g->scan_tmp, &g->big_list, &g->rowcnt, &g->tmp_rp,
-                      &g->tmp_col, &g->tmp_rho, &g->status};
+                      &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho};
     for (DevBuf *b : bufs) release(*b, s);
     if (g->h_status) {
         cudaStreamSynchronize(s);

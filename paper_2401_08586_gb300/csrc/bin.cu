@@ -16,6 +16,7 @@
 //              coordinate x_rel = 2 (x - x_cc) / h_c with x_cc the cell centre,
 //              computed in FP64 and rounded once to FP16 (rel16) and FP32
 //              (rel32); or, for the FP64 cell link-list, the FP64 coordinate.
+#include "profile.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -156,6 +157,8 @@ static unsigned grid_for(long long n, int nt, int sm_count, int per_sm) {
 cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count,
                           cudaStream_t s) {
     const int nt = 192;  // multiple of 2 and 3: each thread keeps one axis
+    ProfScope ps(TAG_BOUNDS, s);
+    note_launch(1);
     k_bounds<<<grid_for(n * dim, nt, sm_count, 8), nt, 0, s>>>(xyz, n * dim, dim, st);
     return cudaGetLastError();
 }
@@ -169,12 +172,22 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
     cudaError_t e = cudaMemsetAsync(cnt, 0, g.ncell * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_hash<<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot);
+    {
+        ProfScope ps(TAG_HASH, s);
+        note_launch(1);
+        k_hash<<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot);
+    }
     e = exclusive_scan_i32(cnt, cell_start, g.ncell, scan_tmp, s);
     if (e != cudaSuccess) return e;
-    k_scatter<<<blocks, nt, 0, s>>>(n, cell_start, cid, slot, orig_id);
+    {
+        ProfScope ps(TAG_SCATTER, s);
+        note_launch(1);
+        k_scatter<<<blocks, nt, 0, s>>>(n, cell_start, cid, slot, orig_id);
+    }
     e = segmented_sort_i32(orig_id, cell_start, g.ncell, big_list, big_count, s);
     if (e != cudaSuccess) return e;
+    ProfScope ps(TAG_CONVERT, s);
+    note_launch(1);
     if (prec == SPH_PREC_FP16_RCLL)
         k_convert<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, rel16, rel32,
                                                             nullptr, check_box);

@@ -26,6 +26,7 @@
 // Phase C (rows): one thread per home particle walks its row in order,
 //   counting neighbours, summing the density in CSR order and (fill mode)
 //   writing the column indices.
+#include "profile.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -589,6 +590,8 @@ static cudaError_t launch_nnps_t(const GridDev &g, int *cnt, const long long *ro
     long long blocks = (long long)sm_count * per_sm;
     if (blocks > g.ncell) blocks = g.ncell;
     if (blocks < 1) blocks = 1;
+    ProfScope ps(MODE == MODE_FILL ? TAG_FILL : TAG_COUNT, s);
+    note_launch(1);
     kern<<<(unsigned)blocks, NT, sb, s>>>(g, cnt, row_ptr, col, cap, rho);
     return cudaGetLastError();
 }
@@ -614,6 +617,8 @@ cudaError_t launch_density(const GridDev &g, int prec, const int *rank, const in
     long long blocks = (g.n + nt - 1) / nt;
     if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
     if (blocks < 1) blocks = 1;
+    ProfScope ps(TAG_DENSITY, s);
+    note_launch(1);
     if (g.dim == 2 && prec == SPH_PREC_FP16_RCLL)
         k_density<2, SPH_PREC_FP16_RCLL><<<(unsigned)blocks, nt, 0, s>>>(g, rank, scell, row_ptr, col, canonical, rho);
     else if (g.dim == 3 && prec == SPH_PREC_FP16_RCLL)
@@ -633,6 +638,8 @@ cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long 
     long long blocks = (n + nt - 1) / nt;
     if (blocks > (long long)sm_count * 8) blocks = (long long)sm_count * 8;
     if (blocks < 1) blocks = 1;
+    ProfScope ps(TAG_CANON, s);
+    note_launch(col == nullptr && rho == nullptr ? 1 : 2);
     k_canon_counts<<<(unsigned)blocks, nt, 0, s>>>(n, rank, rp_cell, cnt_tmp);
     cudaError_t e = exclusive_scan_i64(cnt_tmp, rp, n, scan_tmp, s);
     if (e != cudaSuccess) return e;

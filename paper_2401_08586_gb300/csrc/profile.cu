@@ -1,0 +1,103 @@
+// profile.cu -- launch counting and optional per-kernel CUDA-event timing of
+// the library's own launches (events are recorded on the stream each kernel
+// is launched on, so the times are device times of exactly those kernels).
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "sph_internal.cuh"
+#include "profile.cuh"
+
+namespace sph {
+
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_enabled{0};
+static std::mutex g_mu;
+
+struct Pair {
+    int tag;
+    cudaEvent_t a, b;
+};
+static std::vector<Pair> g_pending;
+static std::vector<cudaEvent_t> g_free;
+static double g_ms[TAG_COUNT_] = {0};
+static long long g_calls[TAG_COUNT_] = {0};
+
+static const char *const g_names[TAG_COUNT_] = {"bounds", "hash",  "scan",    "scatter", "sort",
+                                                "convert", "count", "fill",    "density", "canon",
+                                                "fused",   "batch", "step"};
+
+const char *tag_name(int tag) { return (tag >= 0 && tag < TAG_COUNT_) ? g_names[tag] : ""; }
+
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+long long launch_count() { return g_launches.load(); }
+
+static cudaEvent_t take_event() {
+    if (!g_free.empty()) {
+        cudaEvent_t e = g_free.back();
+        g_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(int tag, cudaStream_t s) : tag_(tag), s_(s), a_(nullptr) {
+    if (!g_enabled.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    a_ = take_event();
+    cudaEventRecord((cudaEvent_t)a_, s_);
+}
+
+ProfScope::~ProfScope() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaEvent_t b = take_event();
+    cudaEventRecord(b, s_);
+    g_pending.push_back({tag_, (cudaEvent_t)a_, b});
+}
+
+static void drain_locked() {
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_ms[p.tag] += ms;
+            g_calls[p.tag] += 1;
+        }
+        g_free.push_back(p.a);
+        g_free.push_back(p.b);
+    }
+    g_pending.clear();
+    cudaGetLastError();
+}
+
+void prof_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_enabled.store(on ? 1 : 0);
+}
+
+void prof_reset() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain_locked();
+    for (int t = 0; t < TAG_COUNT_; ++t) {
+        g_ms[t] = 0;
+        g_calls[t] = 0;
+    }
+}
+
+int prof_read(const char *name, double *ms, long long *calls) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain_locked();
+    for (int t = 0; t < TAG_COUNT_; ++t) {
+        if (strcmp(name, g_names[t]) == 0) {
+            if (ms) *ms = g_ms[t];
+            if (calls) *calls = g_calls[t];
+            return 0;
+        }
+    }
+    return -1;
+}
+
+}  // namespace sph

@@ -1,0 +1,48 @@
+// profile.cuh -- launch counting and per-kernel event timing (profile.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <string.h>
+
+namespace sph {
+
+enum ProfTag {
+    TAG_BOUNDS,
+    TAG_HASH,
+    TAG_SCAN,
+    TAG_SCATTER,
+    TAG_SORT,
+    TAG_CONVERT,
+    TAG_COUNT,
+    TAG_FILL,
+    TAG_DENSITY,
+    TAG_CANON,
+    TAG_FUSED,
+    TAG_BATCH,
+    TAG_STEP,
+    TAG_COUNT_
+};
+
+// Add k to the number of kernels the library has launched.
+void note_launch(int k);
+long long launch_count();
+const char *tag_name(int tag);
+
+// While profiling is enabled, records a CUDA event on `s` at construction and
+// another at destruction; the elapsed time is credited to `tag`.
+class ProfScope {
+   public:
+    ProfScope(int tag, cudaStream_t s);
+    ~ProfScope();
+
+   private:
+    int tag_;
+    cudaStream_t s_;
+    void *a_;
+};
+
+void prof_enable(int on);
+void prof_reset();
+int prof_read(const char *name, double *ms, long long *calls);
+
+}  // namespace sph

@@ -8,6 +8,7 @@
 // segment end behave as +infinity and are simply skipped, so no padding is
 // stored.  Segments of <= 32 keys are sorted in registers by one warp,
 // <= 1024 keys by one warp in shared memory, larger ones by a whole block.
+#include "profile.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -109,6 +110,8 @@ cudaError_t scan_impl(const int *in, OutT *out, long long n, void *tmp, cudaStre
     long long ntile = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntile == 0) ntile = 1;
     long long *sums = (long long *)tmp;
+    ProfScope ps(TAG_SCAN, s);
+    note_launch(3);
     k_tile_sums<<<(unsigned)ntile, SCAN_NT, 0, s>>>(in, n, sums);
     k_scan_sums<<<1, SCAN_NT, 0, s>>>(sums, ntile);
     k_tile_scan<OutT><<<(unsigned)ntile, SCAN_NT, 0, s>>>(in, out, n, sums, ntile);
@@ -217,6 +220,8 @@ template <typename IdxT>
 cudaError_t seg_sort_impl(int *keys, const IdxT *seg, long long nseg, int *big_list,
                           unsigned int *big_count, cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
+    ProfScope ps(TAG_SORT, s);
+    note_launch(2);
     cudaMemsetAsync(big_count, 0, sizeof(unsigned int), s);
     long long blocks = (nseg * 32 + SORT_NT - 1) / SORT_NT;
     if (blocks > 152 * 16) blocks = 152 * 16;

@@ -85,11 +85,20 @@ def load(build_if_missing=False):
         "sph_last_error": [],
         "sph_precision_bands": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "sph_version": [],
+        "sph_search_host": [ctypes.POINTER(sph_params), _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(_vp), _vp],
+        "sph_grid_csr": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                         ctypes.POINTER(ctypes.c_int64)],
+        "sph_profile_enable": [ctypes.c_int],
+        "sph_profile_reset": [],
+        "sph_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+        "sph_launch_count": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_char_p if name == "sph_last_error" else ctypes.c_int
+    lib.sph_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -98,7 +107,8 @@ def exported_symbols():
     """Names of the C-ABI entry points this binding expects."""
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
             "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
-            "sph_precision_bands", "sph_version"]
+            "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
+            "sph_profile_enable", "sph_profile_reset", "sph_profile_read", "sph_launch_count"]
 
 
 def _check(rc):
@@ -177,6 +187,53 @@ def sph_precision_bands():
 
 def sph_version():
     return load().sph_version()
+
+
+def sph_search_host(params, xyz_host, n, rho_host=None, stream=None, grid=None):
+    """xyz_host / rho_host: host numpy arrays or pinned CPU torch tensors
+    (float64 n x dim / float32 n).  Returns (grid handle, nnz)."""
+    g = _vp(grid)
+    nnz = ctypes.c_int64(-1)
+    _check(load().sph_search_host(ctypes.byref(params), _host_ptr(xyz_host), int(n), _host_ptr(rho_host),
+                                  ctypes.byref(nnz), ctypes.byref(g), _stream(stream)))
+    return g.value, nnz.value
+
+
+def sph_grid_csr(grid):
+    """(row_ptr, col, rho) device addresses and nnz of the grid-owned CSR."""
+    a, b, c = _vp(), _vp(), _vp()
+    nnz = ctypes.c_int64()
+    _check(load().sph_grid_csr(grid, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(nnz)))
+    return a.value, b.value, c.value, nnz.value
+
+
+def sph_profile_enable(on=True):
+    _check(load().sph_profile_enable(1 if on else 0))
+
+
+def sph_profile_reset():
+    _check(load().sph_profile_reset())
+
+
+def sph_profile_read(kernel):
+    """(total milliseconds, launches) of one kernel tag since the last reset."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(load().sph_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def sph_launch_count():
+    return load().sph_launch_count()
+
+
+def _host_ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
 
 
 # ---- convenience ------------------------------------------------------------
