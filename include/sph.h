@@ -137,9 +137,11 @@ int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, void *strea
  *   row_ptr      device int64[n+1]: written.  row_ptr[n] = nnz.
  *   col          device int32[col_capacity] or NULL.  NULL: only row_ptr (and
  *                *nnz_out) are produced.
- *   col_capacity entries available in col.  If nnz > col_capacity nothing is
- *                written to col, and the call (or the next synchronising call
- *                when nnz_out is NULL) returns SPH_ERR_CAPACITY.
+ *   col_capacity entries available in col.  If nnz > col_capacity no entry at
+ *                or past col[col_capacity] is written (the contents of col
+ *                are then unspecified; row_ptr is complete), and the call (or
+ *                the next synchronising call when nnz_out is NULL) returns
+ *                SPH_ERR_CAPACITY.
  *   nnz_out      host int64 or NULL.  Non-NULL: the call synchronises `stream`
  *                and stores nnz.  NULL: the call does not synchronise.
  *   rho          device float[n] or NULL.  Non-NULL (and col non-NULL): the
@@ -159,6 +161,14 @@ int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_
  */
 int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, float *rho,
                     void *stream);
+
+/* Per-grid switches (host call, no GPU work).
+ *   SPH_OPT_FUSED (default 1): cell-order FP16-RCLL queries with col != NULL
+ *     run the single-pass search (candidate tests once; CSR offsets found by
+ *     a look-back across cells).  0 selects the two-pass search (count pass,
+ *     row scan, fill pass).  Both give identical results. */
+#define SPH_OPT_FUSED 1
+int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 
 /* Fill *info (host) with the grid's sizes and device pointers.  The pointers
  * stay valid until the grid is re-binned or freed. */

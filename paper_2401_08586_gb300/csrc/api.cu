@@ -25,6 +25,8 @@ cudaError_t launch_nnps(const GridDev &g, int prec, int mode_fill, int *cnt, con
 cudaError_t launch_density(const GridDev &g, int prec, const int *rank, const int *scell,
                            const long long *row_ptr, const int *col, int canonical, float *rho,
                            int sm_count, cudaStream_t s);
+cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, long long cap, float *rho,
+                              unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);
 cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long long *rp_cell,
                          const int *col_cell, const float *rho_cell, int *cnt_tmp, void *scan_tmp,
                          long long *rp, int *col, float *rho, int *big_list, unsigned int *big_count,
@@ -80,7 +82,8 @@ struct sph_grid_s {
     double hc = 0;
     const double *xyz = nullptr;
     DevBuf cell_start, cnt, cid, slot, orig_id, rank, scell, rel16, rel32, x64, scan_tmp, big_list,
-        rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho;
+        rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho, tstate;
+    int fused_enabled = 1;  // single-pass search for cell-order FP16 queries
     long long own_nnz = 0;
     DevStatus *h_status = nullptr;  // pinned host mirror
 };
@@ -406,10 +409,18 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         SPH_TRY(ensure(g->tmp_rp, (n + 1) * sizeof(long long), s));
         rp_cell = P<long long>(g->tmp_rp);
     }
-    SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
-    SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
+    const bool fused = !canonical && col != nullptr && prec == SPH_PREC_FP16_RCLL && g->fused_enabled;
+    if (fused) {
+        // single pass: tests once, row offsets by look-back across cells
+        SPH_TRY(ensure(g->tstate, (size_t)g->ncell * sizeof(unsigned long long), s));
+        SPH_CUDA(launch_nnps_fused(d, rp_cell, col, col_capacity, rho, P<unsigned long long>(g->tstate),
+                                   P<int>(g->rowcnt), g->sm_count, s));
+    } else {
+        SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
+        SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
+    }
     if (!canonical) {
-        if (col)
+        if (col && !fused)
             SPH_CUDA(launch_nnps(d, prec, 1, nullptr, rp_cell, col, col_capacity, rho, g->sm_count, s));
         if (nnz_out) {
             SPH_CUDA(cudaMemcpyAsync(&g->h_status->nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -509,6 +520,16 @@ extern "C" int sph_grid_export(sph_grid_t grid, int32_t *orig_id, int32_t *rank,
     return SPH_OK;
 }
 
+extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (option == SPH_OPT_FUSED) {
+        g->fused_enabled = value != 0;
+        return SPH_OK;
+    }
+    return fail(SPH_ERR_INVALID, "unknown option %d", option);
+}
+
 extern "C" int sph_grid_check(sph_grid_t grid, void *stream) {
     sph_grid_s *g = grid;
     if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
@@ -588,7 +609,8 @@ extern "C" int sph_grid_free(sph_grid_t grid) {
     cudaStream_t s = g->stream;
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
                       &g->rel16, &g->rel32, &g->x64, &g->scan_tmp, &g->big_list, &g->rowcnt, &g->tmp_rp,
-                      &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho};
+                      &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
+                      &g->tstate};
     for (DevBuf *b : bufs) release(*b, s);
     if (g->h_status) {
         cudaStreamSynchronize(s);

@@ -93,6 +93,7 @@ def load(build_if_missing=False):
         "sph_profile_reset": [],
         "sph_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "sph_launch_count": [],
+        "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -108,7 +109,15 @@ def exported_symbols():
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
             "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
-            "sph_profile_enable", "sph_profile_reset", "sph_profile_read", "sph_launch_count"]
+            "sph_profile_enable", "sph_profile_reset", "sph_profile_read", "sph_launch_count",
+            "sph_grid_set_option"]
+
+
+SPH_OPT_FUSED = 1
+
+
+def sph_grid_set_option(grid, option, value):
+    _check(load().sph_grid_set_option(grid, int(option), int(value)))
 
 
 def _check(rc):

