@@ -290,21 +290,25 @@ def main():
         dev_total_s = float(t.item())
     value = world * n * args.steps / dev_total_s
     phase = {}
-    for tag in ("bounds", "hash", "scan", "scatter", "sort", "convert", "count", "fill"):
+    for tag in ("bounds", "hash", "scan", "scatter", "sort", "convert", "count", "fill", "fused"):
         ms, c = sph.sph_profile_read(tag)
-        phase[tag] = {"ms_total": ms, "launches": c}
+        if c:
+            phase[tag] = {"ms_total": ms, "launches": c}
     nnz = int(row_ptr[n].item())
     info = sph.sph_grid_info_get(grid)
 
-    # roofline of the dominant kernel (the fill pass: tests + FP32 re-decision
-    # + fused density + CSR write), algorithmic bytes per launch
-    fill_ms = phase["fill"]["ms_total"] / max(phase["fill"]["launches"], 1)
-    alg_fill = n * (8 + 16 + 8 + 4) + 4 * nnz
+    # roofline of the dominant kernel (the search: FP16 tests + FP32
+    # re-decision + fused density + CSR write), algorithmic bytes per launch:
+    # rel16 8 + rel32 16 + row_ptr 8 + rho 4 per particle, 4 per neighbour
+    dom = "fused" if "fused" in phase else "fill"
+    dom_ms = phase[dom]["ms_total"] / phase[dom]["launches"]
+    alg_dom = n * (8 + 16 + 8 + 4) + 4 * nnz
     peak, peak_src = measured_peaks()
-    achieved = alg_fill / (fill_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_nnps<fill>", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg_fill, "traffic": ncu_traffic(args.workload, "fill")}
+    achieved = alg_dom / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_nnps_fused" if dom == "fused" else "k_nnps<fill>",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "launch_ms": dom_ms, "algorithmic_bytes_per_launch": alg_dom,
+                "traffic": ncu_traffic(args.workload, dom)}
     # whole path: binning 56 B/particle, search + fused density 36 B/particle + 4 B/neighbour
     alg_step = n * (56 + 36) + 4 * nnz
     step_ms_mean = 1e3 * dev_total_s / args.steps

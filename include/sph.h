@@ -163,10 +163,12 @@ int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col,
                     void *stream);
 
 /* Per-grid switches (host call, no GPU work).
- *   SPH_OPT_FUSED (default 1): cell-order FP16-RCLL queries with col != NULL
- *     run the single-pass search (candidate tests once; CSR offsets found by
- *     a look-back across cells).  0 selects the two-pass search (count pass,
- *     row scan, fill pass).  Both give identical results. */
+ *   SPH_OPT_FUSED selects the search of cell-order FP16-RCLL queries with
+ *     col != NULL (all give identical results):
+ *       1 (default) single pass, one warp per 32-particle tile of a row of
+ *         cells, CSR offsets found by a look-back across tiles;
+ *       2 single pass, one thread block per cell, look-back across cells;
+ *       0 two passes (count pass, row scan, fill pass). */
 #define SPH_OPT_FUSED 1
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 

@@ -27,6 +27,11 @@ cudaError_t launch_density(const GridDev &g, int prec, const int *rank, const in
                            int sm_count, cudaStream_t s);
 cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, long long cap, float *rho,
                               unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);
+cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
+                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
+cudaError_t launch_nnps_tile(const GridDev &g, const int4 *tiles, const long long *ntiles_dev, long long ntiles_max,
+                             long long *row_ptr, int *col, long long cap, float *rho, unsigned long long *tstate,
+                             int sm_count, cudaStream_t s);
 cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long long *rp_cell,
                          const int *col_cell, const float *rho_cell, int *cnt_tmp, void *scan_tmp,
                          long long *rp, int *col, float *rho, int *big_list, unsigned int *big_count,
@@ -82,8 +87,9 @@ struct sph_grid_s {
     double hc = 0;
     const double *xyz = nullptr;
     DevBuf cell_start, cnt, cid, slot, orig_id, rank, scell, rel16, rel32, x64, scan_tmp, big_list,
-        rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho, tstate;
-    int fused_enabled = 1;  // single-pass search for cell-order FP16 queries
+        rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho, tstate, scell_x, tcount,
+        toff, tiles;
+    int fused_enabled = 1;  // search variant for cell-order FP16 queries (SPH_OPT_FUSED)
     long long own_nnz = 0;
     DevStatus *h_status = nullptr;  // pinned host mirror
 };
@@ -183,6 +189,7 @@ static GridDev make_dev(sph_grid_s *g) {
     d.rel32 = P<float4>(g->rel32);
     d.x64 = P<double>(g->x64);
     d.orig_id = P<int>(g->orig_id);
+    d.scell_x = P<int>(g->scell_x);
     d.xyz = g->xyz;
     const double kh = g->p.kh, h = g->p.h;
     d.kh2 = kh * kh;
@@ -410,11 +417,25 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         rp_cell = P<long long>(g->tmp_rp);
     }
     const bool fused = !canonical && col != nullptr && prec == SPH_PREC_FP16_RCLL && g->fused_enabled;
-    if (fused) {
-        // single pass: tests once, row offsets by look-back across cells
+    if (fused && g->fused_enabled == 2) {
+        // single pass, one CTA per cell, row offsets by look-back across cells
         SPH_TRY(ensure(g->tstate, (size_t)g->ncell * sizeof(unsigned long long), s));
         SPH_CUDA(launch_nnps_fused(d, rp_cell, col, col_capacity, rho, P<unsigned long long>(g->tstate),
                                    P<int>(g->rowcnt), g->sm_count, s));
+    } else if (fused) {
+        // single pass, one warp per 32-particle row tile, look-back across tiles
+        const long long nrow = (long long)g->nk[1] * g->nk[2];
+        const long long ntiles_max = n / 32 + nrow + 1;
+        SPH_TRY(ensure(g->scell_x, n * sizeof(int), s));
+        SPH_TRY(ensure(g->tcount, nrow * sizeof(int), s));
+        SPH_TRY(ensure(g->toff, (nrow + 1) * sizeof(long long), s));
+        SPH_TRY(ensure(g->tiles, ntiles_max * sizeof(int4), s));
+        SPH_TRY(ensure(g->tstate, ntiles_max * sizeof(unsigned long long), s));
+        d = make_dev(g);
+        SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), P<int>(g->tcount), P<long long>(g->toff),
+                              g->scan_tmp.p, P<int4>(g->tiles), g->sm_count, s));
+        SPH_CUDA(launch_nnps_tile(d, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell, col,
+                                  col_capacity, rho, P<unsigned long long>(g->tstate), g->sm_count, s));
     } else {
         SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
         SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
@@ -524,7 +545,8 @@ extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
     sph_grid_s *g = grid;
     if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
     if (option == SPH_OPT_FUSED) {
-        g->fused_enabled = value != 0;
+        if (value < 0 || value > 2) return fail(SPH_ERR_INVALID, "SPH_OPT_FUSED takes 0, 1 or 2");
+        g->fused_enabled = (int)value;
         return SPH_OK;
     }
     return fail(SPH_ERR_INVALID, "unknown option %d", option);
@@ -610,7 +632,7 @@ extern "C" int sph_grid_free(sph_grid_t grid) {
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
                       &g->rel16, &g->rel32, &g->x64, &g->scan_tmp, &g->big_list, &g->rowcnt, &g->tmp_rp,
                       &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
-                      &g->tstate};
+                      &g->tstate, &g->scell_x, &g->tcount, &g->toff, &g->tiles};
     for (DevBuf *b : bufs) release(*b, s);
     if (g->h_status) {
         cudaStreamSynchronize(s);

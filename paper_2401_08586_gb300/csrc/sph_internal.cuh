@@ -51,6 +51,7 @@ struct GridDev {
     const float4 *rel32;  // per sorted particle: x_rel, y_rel, z_rel, 0
     const double *x64;    // FP64-CLL mode: cell-ordered coordinates, 4 doubles per particle
     const int *orig_id;   // sorted position -> input index
+    const int *scell_x;   // cell x of each sorted particle (row-tile search)
     const double *xyz;    // caller coordinates (input order, n x dim)
     double kh2;           // kh * kh in FP64 (the oracle's threshold)
     float t32_in;         // FP32 tier: r2_u < t32_in  -> neighbour

@@ -28,7 +28,7 @@ def sph():
 def run(sph, xyz, h, kh, order, precision=0, density=True, mass=1.0, box=None, cell_size=0.0, fused=True):
     x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float64)).cuda()
     g = sph.Grid(x, h, kh, order=order, precision=precision, mass=mass, box=box, cell_size=cell_size)
-    sph.sph_grid_set_option(g.handle, sph.SPH_OPT_FUSED, 1 if fused else 0)
+    sph.sph_grid_set_option(g.handle, sph.SPH_OPT_FUSED, int(fused))
     rp, col, rho = g.query(density=density)
     torch.cuda.synchronize()
     out = dict(rp=rp.cpu().numpy(), col=col.cpu().numpy(), rho=None if rho is None else rho.cpu().numpy(),
@@ -93,8 +93,11 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("order,fused", [(0, True), (0, False), (1, False)],
-                         ids=["cell-fused", "cell-twopass", "canonical"])
+VARIANTS = [(0, 1), (0, 2), (0, 0), (1, 0)]
+VARIANT_IDS = ["cell-tile", "cell-cta", "cell-twopass", "canonical"]
+
+
+@pytest.mark.parametrize("order,fused", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_parity_fp16_rcll(sph, case, order, fused):
     xyz, h = CASES[case]()
@@ -120,7 +123,7 @@ def test_exact_ties_power_of_two_lattice(sph):
     assert out["grid"].info().stat_fp64_pairs > 0
 
 
-@pytest.mark.parametrize("order,fused", [(0, True), (0, False), (1, False)])
+@pytest.mark.parametrize("order,fused", VARIANTS, ids=VARIANT_IDS)
 def test_coincident_and_crowded_cells(sph, order, fused):
     """Cells with more than 32 particles (several home batches) and more than
     1024 candidates (several candidate windows); in the single-pass search
@@ -132,14 +135,25 @@ def test_coincident_and_crowded_cells(sph, order, fused):
     check_against_oracle(out, xyz, 0.02, 0.04, order)
 
 
-def test_fused_matches_twopass_bitwise(sph):
-    """The single-pass and two-pass searches give the same CSR and density."""
+@pytest.mark.parametrize("variant", [1, 2])
+def test_fused_matches_twopass(sph, variant):
+    """The single-pass searches give the same CSR as the two-pass search and
+    the same density up to FP32 summation order."""
     ps = W.c2_3d_1m(side=30)
-    a = run(sph, ps.xyz, ps.h, ps.kh, 0, fused=True)
-    b = run(sph, ps.xyz, ps.h, ps.kh, 0, fused=False)
+    a = run(sph, ps.xyz, ps.h, ps.kh, 0, fused=variant)
+    b = run(sph, ps.xyz, ps.h, ps.kh, 0, fused=0)
     assert np.array_equal(a["rp"], b["rp"]) and np.array_equal(a["col"], b["col"])
     rel = np.abs(a["rho"].astype(np.float64) - b["rho"]) / b["rho"]
     assert rel.max() <= 2e-6
+
+
+def test_sparse_rows_several_groups(sph):
+    """Row tiles whose 32 particles span more than four cells (sparse spray)
+    are split into home groups and take the two-step path."""
+    rng = np.random.default_rng(17)
+    xyz = np.vstack([rng.uniform(0, 1, size=(3000, 3)) * [1.0, 0.05, 0.05], rng.uniform(0, 1, size=(2000, 3))])
+    out = run(sph, xyz, 0.004, 0.008, 0, fused=1)
+    check_against_oracle(out, xyz, 0.004, 0.008, 0)
 
 
 def test_empty_input(sph):
