@@ -40,7 +40,6 @@ constexpr int SPANMAX = 4;    // home cells per group along x (keeps |X| < 8)
 constexpr int WIN = 256;      // candidates per staging window
 constexpr int CMAX = 1024;    // candidates per super-window (bitmask length)
 constexpr int NWORD = CMAX / 32;
-constexpr int STGCAP = 4096;  // staged column slots per tile
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
@@ -51,8 +50,6 @@ struct TileSmem {
     uint4 pw[WIN / 2];          // FP16 pairs: word (g*16 + b) = candidates 32g + b (lo), 32g + 16 + b (hi)
     float4 f32[WIN];            // FP32 frame coordinates, candidate index j in .w
     unsigned int S[TW][NWORD + 1];
-    int jall[CMAX];
-    unsigned short stg[STGCAP];
     int rstart[9], roff[10], rdy[9], rdz[9], rcb[9][8];
     int C;
     int nbm1;  // internal cell boundaries per candidate row + 1
@@ -201,7 +198,6 @@ __device__ __forceinline__ void stage_window(TileSmem &S, const GridDev &g, int 
             hy = __high2half(xy);
             hz = __hadd(__low2half(as_h2(q16.y)), __float2half_rn(sz));
             f = make_float4(__fadd_rn(r32.x, sx), __fadd_rn(r32.y, sy), __fadd_rn(r32.z, sz), __int_as_float(j));
-            S.jall[p - s0] = j;
         } else {
             hx = hy = hz = __float2half_rn(30000.f);
             f = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
@@ -411,10 +407,11 @@ __global__ void __launch_bounds__(32) k_nnps_tile(GridDev g, const int4 *__restr
                 }
                 if (t == ntiles - 1 && lane == 0) row_ptr[g.n] = pre + agg;
                 if (simple && wc && col != nullptr) {
-                    // emit rows from the kept bits: staged, then copied out
+                    // emit each row from its kept bits; the column index comes
+                    // from the candidate row table (rows are contiguous ranges)
                     const int nw = (S.C + 31) >> 5;
-                    const bool fits = agg <= STGCAP;
-                    int pos = roff, gi = 0;
+                    long long pos = pre + roff;
+                    int gi = 0;
                     unsigned int w = (mine && nw > 0) ? S.S[lane][0] : 0u;
                     while (true) {
                         while (w == 0u && gi < nw) {
@@ -426,14 +423,12 @@ __global__ void __launch_bounds__(32) k_nnps_tile(GridDev g, const int4 *__restr
                             const int b = __ffs(w) - 1;
                             w &= w - 1u;
                             const int p = gi * 32 + b;
-                            if (fits) S.stg[pos] = (unsigned short)p;
-                            else col[pre + pos] = S.jall[p];
-                            ++pos;
+                            int r = 0;
+#pragma unroll
+                            for (int q = 1; q < 9; ++q) r = (p >= S.roff[q]) ? q : r;
+                            col[pos++] = S.rstart[r] + (p - S.roff[r]);
                         }
                     }
-                    __syncwarp();
-                    if (fits)
-                        for (int e = lane; e < agg; e += 32) col[pre + e] = S.jall[S.stg[e]];
                     __syncwarp();
                 }
                 if (!simple) {
