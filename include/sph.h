@@ -162,6 +162,44 @@ int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_
 int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, float *rho,
                     void *stream);
 
+/*
+ * The neighbour search of sph_nnps_query (cell order, FP16-RCLL, fused
+ * density, single pass over row tiles) for callers that cannot allocate
+ * device memory when they call it.  Typical such callers: a process whose
+ * device memory is all handed out up front by its own allocator or an HBM
+ * budget (a cudaMalloc from inside the library would fail or break that
+ * accounting), and latency-critical loops that cannot afford the implicit
+ * synchronisation and unbounded time of an allocation.  sph_nnps_query may
+ * grow grid-owned buffers with cudaMallocAsync; this call never allocates
+ * and calls no allocating routine.  (The paper has no counterpart; this is an
+ * interface addition.)
+ *
+ * Its working memory (cell index per particle, tile list, look-back state:
+ * about 7.1 MiB) is one fixed array inside the library.  Every GPU that loads
+ * the library holds that array until the process exits.  The first call on
+ * each device looks up the array's device address with
+ * cudaGetSymbolAddress (no allocation) and caches it; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (the call clears what must start at zero), so calls
+ * whose GPU work overlaps -- different streams, or concurrent host threads on
+ * one device -- race and give wrong results: serialise them.
+ *
+ *   grid         binned by sph_bin_cells with precision SPH_PREC_FP16_RCLL and
+ *                order SPH_ORDER_CELL (the grid's own buffers are read, not
+ *                grown).
+ *   row_ptr      device int64[n+1], written; row_ptr[n] = nnz.
+ *   col          device int32[col_capacity], written (cell-sorted indices,
+ *                ascending per row); nothing at or past col_capacity.
+ *   rho          device float[n] or NULL: fused density, cell order.
+ * The call does not synchronise; an nnz above col_capacity is reported as
+ * SPH_ERR_CAPACITY by the next sph_grid_check.
+ * Limits: n <= 1048576 particles and nk[1] * nk[2] <= 65536 rows of cells;
+ * larger grids, another precision or order, or a NULL row_ptr/col give
+ * SPH_ERR_INVALID without any GPU work.
+ */
+int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity, float *rho,
+                          void *stream);
+
 /* Per-grid switches (host call, no GPU work).
  *   SPH_OPT_FUSED selects the search of cell-order FP16-RCLL queries with
  *     col != NULL (all give identical results):

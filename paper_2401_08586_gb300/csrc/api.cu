@@ -625,6 +625,30 @@ extern "C" int sph_profile_read(const char *kernel, double *total_ms, int64_t *l
 
 extern "C" int64_t sph_launch_count(void) { return launch_count(); }
 
+namespace sph {
+
+int grid_view(sph_grid_t grid, GridView *v) {
+    sph_grid_s *g = grid;
+    if (!g || !v) return fail(SPH_ERR_INVALID, "grid is NULL");
+    v->d = make_dev(g);
+    v->scell = P<int>(g->scell);
+    v->sm_count = g->sm_count;
+    v->precision = g->p.precision;
+    v->order = g->p.order;
+    v->n = g->n;
+    v->nrow = (long long)g->nk[1] * g->nk[2];
+    return SPH_OK;
+}
+
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+void reset_counters_async(DevStatus *st, cudaStream_t s) {
+    note_launch(1);
+    k_status_reset_counters<<<1, 1, 0, s>>>(st);
+}
+
+}  // namespace sph
+
 extern "C" int sph_grid_free(sph_grid_t grid) {
     sph_grid_s *g = grid;
     if (!g) return SPH_OK;

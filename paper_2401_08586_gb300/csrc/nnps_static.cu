@@ -1,0 +1,120 @@
+// nnps_static.cu -- sph_nnps_query_static: the single-pass row-tile search
+// without any device allocation, for callers that must not allocate at the
+// time of the call (see include/sph.h).
+//
+// The search's working memory (cell x of every particle, the tile list and
+// its row offsets, the look-back state of the tiles, the scan's tile sums)
+// lives in one fixed file-scope device array.  Host code must not hand the
+// array's name to a kernel (in host code it names a host-side stand-in), so
+// the first call on each device, with that device current, asks the runtime
+// for the array's device address and caches it.
+#include <mutex>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
+                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
+cudaError_t launch_nnps_tile(const GridDev &g, const int4 *tiles, const long long *ntiles_dev, long long ntiles_max,
+                             long long *row_ptr, int *col, long long cap, float *rho, unsigned long long *tstate,
+                             int sm_count, cudaStream_t s);
+
+namespace {
+
+constexpr long long STATIC_MAX_N = 1LL << 20;     // particles
+constexpr long long STATIC_MAX_ROWS = 1LL << 16;  // rows of cells (ny * nz)
+constexpr long long STATIC_MAX_TILES = STATIC_MAX_N / 32 + STATIC_MAX_ROWS + 1;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Layout of the array.
+constexpr size_t OFF_SCELLX = 0;
+constexpr size_t OFF_TCOUNT = align256(OFF_SCELLX + STATIC_MAX_N * sizeof(int));
+constexpr size_t OFF_TOFF = align256(OFF_TCOUNT + STATIC_MAX_ROWS * sizeof(int));
+constexpr size_t OFF_TILES = align256(OFF_TOFF + (STATIC_MAX_ROWS + 1) * sizeof(long long));
+constexpr size_t OFF_TSTATE = align256(OFF_TILES + STATIC_MAX_TILES * sizeof(int4));
+constexpr size_t OFF_SCAN = align256(OFF_TSTATE + STATIC_MAX_TILES * sizeof(unsigned long long));
+constexpr size_t STATIC_SCRATCH_BYTES = align256(OFF_SCAN + 64 * 1024);
+
+__device__ __align__(256) unsigned char g_query_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_addr_mu;
+void *g_addr[MAX_DEVICES] = {nullptr};
+
+// Device address of the array on the current device (looked up once).
+int scratch_address(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SPH_ERR_CUDA, "cudaGetDevice failed");
+    }
+    if (dev < 0 || dev >= MAX_DEVICES) return set_error(SPH_ERR_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_query_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return set_error(SPH_ERR_CUDA, "cudaGetSymbolAddress of the static search scratch failed");
+        }
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return SPH_OK;
+}
+
+}  // namespace
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity,
+                                     float *rho, void *stream) {
+    GridView v;
+    int rc = grid_view(grid, &v);
+    if (rc != SPH_OK) return rc;
+    if (!row_ptr || !col || col_capacity < 0) return set_error(SPH_ERR_INVALID, "row_ptr and col are required");
+    if (v.precision != SPH_PREC_FP16_RCLL || v.order != SPH_ORDER_CELL)
+        return set_error(SPH_ERR_INVALID, "sph_nnps_query_static needs a grid binned with SPH_PREC_FP16_RCLL "
+                                          "and SPH_ORDER_CELL");
+    if (v.n > STATIC_MAX_N)
+        return set_error(SPH_ERR_INVALID, "sph_nnps_query_static handles at most 1048576 particles");
+    if (v.nrow > STATIC_MAX_ROWS)
+        return set_error(SPH_ERR_INVALID, "sph_nnps_query_static handles at most 65536 rows of cells (ny * nz)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (v.n == 0) {
+        if (cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(SPH_ERR_CUDA, "cudaMemsetAsync failed");
+        }
+        return SPH_OK;
+    }
+    void *base = nullptr;
+    rc = scratch_address(&base);
+    if (rc != SPH_OK) return rc;
+    unsigned char *b = static_cast<unsigned char *>(base);
+    int *scell_x = reinterpret_cast<int *>(b + OFF_SCELLX);
+    int *tcount = reinterpret_cast<int *>(b + OFF_TCOUNT);
+    long long *toff = reinterpret_cast<long long *>(b + OFF_TOFF);
+    int4 *tiles = reinterpret_cast<int4 *>(b + OFF_TILES);
+    unsigned long long *tstate = reinterpret_cast<unsigned long long *>(b + OFF_TSTATE);
+    void *scan_tmp = b + OFF_SCAN;
+    GridDev d = v.d;
+    d.scell_x = scell_x;
+    const long long ntiles_max = v.n / 32 + v.nrow + 1;
+    // the tile ticket counter must start at zero; the look-back state is
+    // cleared by the launcher; everything else is fully rewritten
+    reset_counters_async(d.status, s);
+    cudaError_t e = launch_tiles(d, v.scell, scell_x, tcount, toff, scan_tmp, tiles, v.sm_count, s);
+    if (e == cudaSuccess)
+        e = launch_nnps_tile(d, tiles, toff + v.nrow, ntiles_max, reinterpret_cast<long long *>(row_ptr), col,
+                             col_capacity, rho, tstate, v.sm_count, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SPH_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return SPH_OK;
+}

@@ -89,6 +89,21 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double hc, int nk
     return (int)t;
 }
 
+// What another translation unit of the library may see of a grid
+// (filled by grid_view in api.cu).
+struct GridView {
+    GridDev d;
+    const int *scell;  // linear cell id of each sorted particle
+    int sm_count;
+    int precision;
+    int order;
+    long long n;
+    long long nrow;    // rows of cells along x: nk[1] * nk[2]
+};
+int grid_view(sph_grid_t grid, GridView *v);
+int set_error(int code, const char *msg);
+void reset_counters_async(DevStatus *st, cudaStream_t s);
+
 // ---- launch helpers (implemented in scan.cu / sort.cu) --------------------
 
 // Exclusive scan of int32 counts into int32 (cell starts) or int64 (row

@@ -94,6 +94,7 @@ def load(build_if_missing=False):
         "sph_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "sph_launch_count": [],
         "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
+        "sph_nnps_query_static": [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -110,7 +111,14 @@ def exported_symbols():
             "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_reset", "sph_profile_read", "sph_launch_count",
-            "sph_grid_set_option"]
+            "sph_grid_set_option", "sph_nnps_query_static"]
+
+
+def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=None):
+    """The search without any device allocation (working memory is a fixed
+    array inside the library); see include/sph.h for its limits."""
+    _check(load().sph_nnps_query_static(grid, _ptr(row_ptr), _ptr(col), int(col_capacity), _ptr(rho),
+                                        _stream(stream)))
 
 
 SPH_OPT_FUSED = 1
