@@ -7,26 +7,28 @@
 //
 // Per home group (the tile's particles whose cells span at most SPANMAX
 // consecutive x-cells; normally the whole tile):
-//   candidates = the 3^d x-rows of cells around the group's cells (each a
-//   contiguous range of the sorted arrays), cell x-range widened by one.
-//   Coordinates are cell-relative (Eq. 6) re-expressed in the frame of the
-//   group's middle cell: X = x_rel + 2 (c_x - x_mid), Y = y_rel + 2 dy,
-//   Z = z_rel + 2 dz (units of u = h_c / 2), so a pair's difference is the
-//   Eq. 7 distance (scale h_c / 2).
-//   1. stage a window of candidates in shared memory, two per half2 word;
-//   2. FP16 test (all lanes, candidates broadcast): e = ((dx^2 - T) + dy^2)
-//      + dz^2 with half2 FMAs; e < tau16 marks a "maybe" pair in the lane's
-//      row bitmask (bit order = candidate order = ascending column);
-//   3. each lane walks its own maybe bits: FP32 distance from the FP32
-//      relative coordinates, decision with the FP32 band (FP64 definition
-//      inside it), neighbour count and density sum (Eq. 3) in CSR order;
-//      rejected bits are cleared.
-// Then the tile's neighbour total is published and the CSR offset of the tile
-// found by a decoupled look-back over earlier tiles; each lane writes its row
-// pointer and density, emits its row into a shared staging buffer (candidate
-// slots), and the warp copies the staged columns out coalesced.
-// Tiles with several home groups or more than CMAX candidates run the same
-// steps twice (count, then emit straight to their rows after the look-back).
+//   * the candidates are the 3^d x-rows of cells around the group's cells
+//     (each a contiguous range of the sorted arrays), x-range widened by one
+//     cell; coordinates are the cell-relative ones of Eq. 6 re-expressed in
+//     the frame of the group's middle cell, X = x_rel + 2 (c_x - x_mid),
+//     Y = y_rel + 2 dy, Z = z_rel + 2 dz (units of u = h_c / 2), so a pair's
+//     difference is the Eq. 7 distance with the scale h_c / 2;
+//   * cull: candidates farther than kh (plus a margin) from the bounding box
+//     of the group's particles cannot be anybody's neighbour and are dropped;
+//     the rest are compacted in candidate order (ascending column);
+//   * stage a window of kept candidates in shared memory, two per half2 word;
+//   * FP16 test (all lanes, candidates broadcast): e = ((dx^2 - T) + dy^2)
+//     + dz^2 with half2 FMAs; e < tau16 sets the candidate's bit in the
+//     lane's row bitmask;
+//   * each lane walks its own bits: FP32 distance from the FP32 relative
+//     coordinates, FP32 band decision (FP64 definition inside the band),
+//     neighbour count and density sum (Eq. 3) in CSR order; rejected bits are
+//     cleared.
+// Then the tile's neighbour total is published and its CSR offset found by a
+// decoupled look-back over earlier tiles; each lane writes its row pointer
+// and density, and emits its row from the kept bits.  Tiles with several
+// home groups or more than CMAX kept candidates run the steps twice (count,
+// then emit straight to their rows after the look-back).
 #include "nnps_common.cuh"
 
 namespace sph {
@@ -37,9 +39,11 @@ namespace {
 
 constexpr int TW = 32;        // rows per tile
 constexpr int SPANMAX = 4;    // home cells per group along x (keeps |X| < 8)
-constexpr int WIN = 256;      // candidates per staging window
-constexpr int CMAX = 1024;    // candidates per super-window (bitmask length)
+constexpr int WIN = 256;      // kept candidates per staging window
+constexpr int CMAX = 1024;    // kept candidates per pass (bitmask length)
 constexpr int NWORD = CMAX / 32;
+constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the culling test
+constexpr int STG_SLOTS = (WIN / 2 * 16 + WIN * 16) / 2;  // 16-bit output slots in pw + f32
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
@@ -47,16 +51,34 @@ constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 constexpr int LOOKBACK_SPIN_LIMIT = 1 << 20;
 
 struct TileSmem {
-    uint4 pw[WIN / 2];          // FP16 pairs: word (g*16 + b) = candidates 32g + b (lo), 32g + 16 + b (hi)
-    float4 f32[WIN];            // FP32 frame coordinates, candidate index j in .w
+    // pw and f32 are contiguous: after the last window they hold the tile's
+    // staged output (16-bit kept-candidate slots), STG_SLOTS of them
+    uint4 pw[WIN / 2];  // FP16 pairs: word (g*16 + b) = kept candidates 32g + b (lo), 32g + 16 + b (hi)
+    float4 f32[WIN];    // FP32 frame coordinates, candidate index j in .w
     unsigned int S[TW][NWORD + 1];
-    int rstart[9], roff[10], rdy[9], rdz[9], rcb[9][8];
-    int C;
-    int nbm1;  // internal cell boundaries per candidate row + 1
+    int jall[CMAX];            // kept candidates: sorted index
+    unsigned char code[CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5
+    int selfpos[TW];           // kept slot of each lane's own particle (-1: not in this fill)
+    int rstart[9], rlen[9], rb[9][8];
 };
 
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
     return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// P(R) of Eq. 3 without alpha_d, branch-free: 2/3 - R^2 + R^3/2 on [0, 1),
+// (2 - R)^3 / 6 on [1, 2), 0 beyond.
+__device__ __forceinline__ float w_poly_bf(float R) {
+    const float t = fmaxf(2.f - R, 0.f);
+    const float w2 = t * t * t * (1.f / 6.f);
+    const float w1 = fmaf(R * R, fmaf(0.5f, R, -1.f), 2.f / 3.f);
+    return R < 1.f ? w1 : w2;
 }
 
 // Publish this tile's total and return the sum over all earlier tiles.
@@ -101,96 +123,141 @@ __device__ __forceinline__ long long look_back(unsigned long long *tstate, long 
     return excl;
 }
 
-__device__ __forceinline__ unsigned int tau16_bits(int mx) {
-    // FP16 band in u^2 for frame coordinates |X| <= mx (see sph_precision_bands):
-    // |X| < 4 -> 0.03, |X| < 8 -> 0.06.
-    const __half t = __float2half_rn(mx < 4 ? 0.03f : 0.06f);
-    return h2_bits(__halves2half2(t, t));
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-// Everything one lane needs about its home particle.
+// Everything one lane needs about its home particle in the current group.
 struct Home {
-    int i;           // sorted index
-    int x;           // cell x
-    __half2 X, Y, Z; // FP16 frame coordinates, splatted
+    int i;            // sorted index
+    int x;            // cell x
+    __half2 X, Y, Z;  // FP16 frame coordinates, splatted
     float x32, y32, z32;
 };
 
-enum { PASS_SINGLE = 0, PASS_COUNT = 1, PASS_EMIT = 2 };
+// One home group: its cells, frame and candidate rows.
+struct Group {
+    int xa, xb, xm, xlo, xhi, nb;  // nb = cell boundaries per candidate row
+    float lo[3], hi[3];            // bounding box of the group's particles (frame, FP32)
+    unsigned int tau;              // FP16 band (half2 bits)
+};
 
-// Candidate row table of a home group (cells [xa, xb] of row (cy, cz)).
+// Candidate row table of a group (cells [xa, xb] of row (cy, cz)).
 template <int DIM>
-__device__ __forceinline__ void group_rows(TileSmem &S, const GridDev &g, int cy, int cz, int xa, int xb) {
+__device__ __forceinline__ void group_rows(TileSmem &S, const GridDev &g, int cy, int cz, const Group &G) {
     constexpr int NROWS = DIM == 3 ? 9 : 3;
     const int lane = threadIdx.x & 31;
     const int nx = g.nk[0], ny = g.nk[1], nz = g.nk[2];
-    const int x_lo = max(xa - 1, 0), x_hi = min(xb + 1, nx - 1);
-    const int nb = x_hi - x_lo + 2;  // boundaries per row (<= SPANMAX + 3)
     for (int e = lane; e < 9 * 8; e += 32) {
         const int r = e >> 3, k = e & 7;
-        int v = 0;
-        if (r < NROWS && k < nb) {
+        int v = -1;
+        if (r < NROWS && k < G.nb) {
             const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
             const int dz = DIM == 3 ? (r / 3) - 1 : 0;
             const int yy = cy + dy, zz = cz + dz;
-            if (yy >= 0 && yy < ny && zz >= 0 && zz < nz)
-                v = g.cell_start[((long long)zz * ny + yy) * nx + x_lo + k];
-            else
-                v = -1;
+            if (yy >= 0 && yy < ny && zz >= 0 && zz < nz) v = g.cell_start[((long long)zz * ny + yy) * nx + G.xlo + k];
         }
-        S.rcb[r][k] = v;
+        S.rb[r][k] = v;
     }
     __syncwarp();
-    int len = 0, start = 0, dy = 0, dz = 0;
     if (lane < 9) {
         const int r = lane;
-        if (r < NROWS) {
-            dy = DIM == 3 ? (r % 3) - 1 : r - 1;
-            dz = DIM == 3 ? (r / 3) - 1 : 0;
-            if (S.rcb[r][0] >= 0) {
-                start = S.rcb[r][0];
-                len = S.rcb[r][nb - 1] - start;
-            }
-        }
-        S.rstart[r] = start;
-        S.rdy[r] = dy;
-        S.rdz[r] = dz;
-    }
-    int inc = len;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    if (lane < 9) S.roff[lane] = inc - len;
-    if (lane == 8) {
-        S.roff[9] = inc;
-        S.C = inc;
-        S.nbm1 = nb - 1;
+        const int a = S.rb[r][0];
+        S.rstart[r] = a >= 0 ? a : 0;
+        S.rlen[r] = a >= 0 ? S.rb[r][G.nb - 1] - a : 0;
     }
     __syncwarp();
 }
 
-// Stage candidates [w0, w0 + wc) (window-local slots 0..wc-1; the rest of the
-// window is padded far away) and their indices into jall[w0 - s0 + .].
-__device__ __forceinline__ void stage_window(TileSmem &S, const GridDev &g, int w0, int wc, int s0, int xlo,
-                                             int xm) {
+// Cull and compact candidates of the group, resuming at (cur_r, cur_base),
+// until the union is exhausted or the kept list cannot take another 32.
+// Returns the number kept; advances the cursor.
+template <int DIM>
+__device__ __forceinline__ int cull_fill(TileSmem &S, const GridDev &g, const Group &G, float cullT, int &cur_r,
+                                         int &cur_base, int p0, int nhome) {
+    constexpr int NROWS = DIM == 3 ? 9 : 3;
     const int lane = threadIdx.x & 31;
+    S.selfpos[lane] = -1;
+    __syncwarp();
+    int kept = 0;
+    while (cur_r < NROWS) {
+        const int len = S.rlen[cur_r];
+        if (cur_base >= len) {
+            ++cur_r;
+            cur_base = 0;
+            continue;
+        }
+        if (kept + 64 > CMAX) break;
+        const int r = cur_r;
+        const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
+        const int dz = DIM == 3 ? (r / 3) - 1 : 0;
+        // two chunks of 32 per step so that both loads are in flight together
+        int jk[2], ox[2];
+        bool valid[2];
+        uint2 q[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int k = cur_base + 32 * u + lane;
+            valid[u] = k < len;
+            jk[u] = S.rstart[r] + k;
+            q[u] = valid[u] ? g.rel16[jk[u]] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            int cxo = 0;
+#pragma unroll
+            for (int qq = 1; qq < 6; ++qq) cxo += (qq < G.nb - 1 && jk[u] >= S.rb[r][qq]) ? 1 : 0;
+            ox[u] = G.xlo + cxo - G.xm;  // frame cell offset in x, |ox| <= 3
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            bool keep = false;
+            if (valid[u]) {
+                const float2 xy = __half22float2(as_h2(q[u].x));
+                const float x = xy.x + 2.f * (float)ox[u], y = xy.y + 2.f * (float)dy;
+                const float z = __low2float(as_h2(q[u].y)) + 2.f * (float)dz;
+                const float ex = fmaxf(fmaxf(G.lo[0] - x, x - G.hi[0]), 0.f);
+                const float ey = fmaxf(fmaxf(G.lo[1] - y, y - G.hi[1]), 0.f);
+                const float ez = fmaxf(fmaxf(G.lo[2] - z, z - G.hi[2]), 0.f);
+                keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < cullT;
+            }
+            const unsigned int m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = kept + __popc(m & ((1u << lane) - 1u));
+                S.jall[pos] = jk[u];
+                S.code[pos] = (unsigned char)((ox[u] + 3) | ((dy + 1) << 3) | ((dz + 1) << 5));
+                // the tile's own particles are the contiguous range [p0, p0 + nhome)
+                if (jk[u] >= p0 && jk[u] < p0 + nhome) S.selfpos[jk[u] - p0] = pos;
+            }
+            kept += __popc(m);
+        }
+        cur_base += 64;
+    }
+    __syncwarp();
+    return kept;
+}
+
+// Stage kept candidates [w0, w0 + wc) into the window (slots past wc padded
+// far away).
+__device__ __forceinline__ void stage_window(TileSmem &S, const GridDev &g, int w0, int wc) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
     for (int k = lane; k < WIN; k += 32) {
         __half hx, hy, hz;
         float4 f;
         if (k < wc) {
-            const int p = w0 + k;
-            int r = 0;
-#pragma unroll
-            for (int q = 1; q < 9; ++q) r = (p >= S.roff[q]) ? q : r;
-            const int j = S.rstart[r] + (p - S.roff[r]);
-            int cxo = 0;  // cell x offset from x_lo: internal boundaries passed
-            const int nbm1 = S.nbm1;
-#pragma unroll
-            for (int q = 1; q < 7; ++q) cxo += (q < nbm1 && j >= S.rcb[r][q]) ? 1 : 0;
-            const float sx = 2.f * (float)(xlo + cxo - xm);
-            const float sy = 2.f * (float)S.rdy[r], sz = 2.f * (float)S.rdz[r];
+            const int j = S.jall[w0 + k];
+            const unsigned int c = S.code[w0 + k];
+            const float sx = 2.f * (float)((int)(c & 7u) - 3);
+            const float sy = 2.f * (float)((int)((c >> 3) & 3u) - 1);
+            const float sz = 2.f * (float)((int)((c >> 5) & 3u) - 1);
             const uint2 q16 = g.rel16[j];
             const float4 r32 = g.rel32[j];
             const __half2 xy = __hadd2(as_h2(q16.x), __floats2half2_rn(sx, sy));
@@ -212,16 +279,18 @@ __device__ __forceinline__ void stage_window(TileSmem &S, const GridDev &g, int 
     __syncwarp();
 }
 
-// FP16 tests of the window against the lane's home particle: one bit per
-// candidate, written to S.S[lane][wbase + g] for the WIN/32 words g.
+// FP16 tests of the window (nwin words of 32) against the lane's home
+// particle; bit per kept candidate into S.S[lane][wbase + gi].  The lane's
+// own particle (window slot self_slot, or -1) is left out.
 template <int DIM>
-__device__ __forceinline__ void test_window(TileSmem &S, const Home &h, bool active, unsigned int negT,
-                                            unsigned int tau, int wbase) {
+__device__ __forceinline__ unsigned int test_window(TileSmem &S, const Home &h, bool active, unsigned int negT,
+                                                    unsigned int tau, int wbase, int nwin, int self_slot) {
     const int lane = threadIdx.x & 31;
     const __half2 nT = as_h2(negT);
     const __half2 tv = as_h2(tau);
+    unsigned int nem = 0;  // non-empty words, returned for the walk
 #pragma unroll 1
-    for (int gi = 0; gi < WIN / 32; ++gi) {
+    for (int gi = 0; gi < nwin; ++gi) {
         unsigned int word = 0;
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
@@ -236,67 +305,174 @@ __device__ __forceinline__ void test_window(TileSmem &S, const Home &h, bool act
             }
             word |= __hlt2_mask(e, tv) & ((1u << b) | (1u << (16 + b)));
         }
-        S.S[lane][wbase + gi] = active ? word : 0u;
+        if ((self_slot >> 5) == gi) word &= ~(1u << (self_slot & 31));
+        word = active ? word : 0u;
+        S.S[lane][wbase + gi] = word;
+        nem |= (word != 0u ? 1u : 0u) << gi;
+    }
+    __syncwarp();
+    return nem;
+}
+
+enum { PASS_COUNT = 0, PASS_EMIT = 1 };
+
+// Walk the lane's bits in words [wbase, wbase + nw) of the window: FP32
+// re-decision (FP64 inside the band) and density; rejected bits cleared.
+// PASS_EMIT writes the neighbours to col[rp + cnt] instead of summing.
+// Up to WB set bits of the lane's words [wbase + gi, wbase + nw), in order:
+// positions p[k] (window-local candidate slots) with v[k] marking valid ones.
+// nem: the lane's words still to visit that hold at least one bit (bit gi for
+// word wbase + gi), so advancing to the next word needs no loop.
+template <int WB>
+__device__ __forceinline__ void next_bits(const TileSmem &S, int lane, int wbase, unsigned int &nem, int &gi,
+                                          unsigned int &w, int (&p)[WB], bool (&v)[WB]) {
+#pragma unroll
+    for (int k = 0; k < WB; ++k) {
+        if (w == 0u && nem != 0u) {
+            gi = __ffs(nem) - 1;
+            nem &= nem - 1u;
+            w = S.S[lane][wbase + gi];
+        }
+        v[k] = w != 0u;
+        p[k] = gi * 32 + (__ffs(w) - 1);
+        w &= w - 1u;
+    }
+}
+
+constexpr int WALK_BATCH = 4;  // bits in flight per lane (independent loads and arithmetic)
+
+// The FP64 definition for the rare pairs inside the FP32 band.  Kept out of
+// line so that its global loads and FP64 arithmetic are never hoisted into
+// the walk loop (FP64 throughput on this part is a small fraction of FP32).
+template <int DIM>
+__device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
+    const int oi = g.orig_id[i], oj = g.orig_id[j];
+    return r2_fp64(DIM, g.xyz + (long long)oi * DIM, g.xyz + (long long)oj * DIM) < g.kh2;
+}
+
+// The lane's own particle has been removed from its bits by test_window, so
+// every remaining bit is a pair j != i.  The common case (FP32 says
+// "neighbour") runs without branches; pairs the FP32 tier rejects or leaves
+// in its band go through a warp-uniform slow path.
+template <int DIM, int PASS>
+__device__ __forceinline__ void walk_window(TileSmem &S, const GridDev &g, const Home &h, int wbase,
+                                            unsigned int nem, int &cnt, float &acc, int *col, long long rp,
+                                            unsigned int &n32, unsigned int &n64) {
+    const int lane = threadIdx.x & 31;
+    int gi = 0;
+    unsigned int w = 0u;
+    while (true) {
+        int p[WALK_BATCH];
+        bool v[WALK_BATCH];
+        next_bits<WALK_BATCH>(S, lane, wbase, nem, gi, w, p, v);
+        if (!__any_sync(0xffffffffu, v[0])) break;
+        float r2[WALK_BATCH];
+        int jj[WALK_BATCH];
+        bool in[WALK_BATCH];
+        bool odd = false;
+#pragma unroll
+        for (int k = 0; k < WALK_BATCH; ++k) {
+            const float4 c = S.f32[v[k] ? p[k] : 0];
+            jj[k] = __float_as_int(c.w);
+            const float d0 = __fsub_rn(c.x, h.x32);
+            const float d1 = __fsub_rn(c.y, h.y32);
+            const float d2 = __fsub_rn(c.z, h.z32);
+            r2[k] = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
+            in[k] = v[k] && r2[k] < g.t32_in;
+            odd |= v[k] && !in[k];
+        }
+        if (__any_sync(0xffffffffu, odd)) {
+#pragma unroll
+            for (int k = 0; k < WALK_BATCH; ++k) {
+                if (v[k] && !in[k]) {
+                    if (r2[k] <= g.t32_out) {
+                        ++n64;
+                        in[k] = fp64_tier<DIM>(g, h.i, jj[k]);
+                    } else {
+                        ++n32;
+                    }
+                    if (!in[k]) S.S[lane][wbase + (p[k] >> 5)] &= ~(1u << (p[k] & 31));
+                }
+            }
+        }
+        if (PASS == PASS_EMIT) {
+#pragma unroll
+            for (int k = 0; k < WALK_BATCH; ++k)
+                if (in[k]) col[rp + cnt++] = jj[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < WALK_BATCH; ++k) {
+                const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
+                acc += in[k] ? wk : 0.f;
+                cnt += in[k] ? 1 : 0;
+            }
+        }
     }
     __syncwarp();
 }
 
-// Walk the lane's maybe bits of words [wbase, wbase + nw): FP32 re-decision
-// (FP64 inside the band), density; clears rejected bits.  In PASS_EMIT the
-// neighbours are written straight to col[rp + cnt].
+// Set up a home group of lanes [gs, ge): frame, bounding box, band, rows.
+template <int DIM>
+__device__ __forceinline__ void group_setup(TileSmem &S, const GridDev &g, Home &h, bool act, int cy, int cz, int gs,
+                                            int ge, Group &G) {
+    const int nx = g.nk[0];
+    G.xa = __shfl_sync(0xffffffffu, h.x, gs);
+    G.xb = __shfl_sync(0xffffffffu, h.x, ge - 1);
+    G.xm = (G.xa + G.xb) >> 1;
+    G.xlo = max(G.xa - 1, 0);
+    G.xhi = min(G.xb + 1, nx - 1);
+    G.nb = G.xhi - G.xlo + 2;
+    const uint2 q = g.rel16[min(h.i, g.n - 1)];
+    const float4 r = g.rel32[min(h.i, g.n - 1)];
+    const float sx = 2.f * (float)(h.x - G.xm);
+    const __half X = __hadd(__low2half(as_h2(q.x)), __float2half_rn(sx));
+    h.X = __halves2half2(X, X);
+    h.Y = __high2half2(as_h2(q.x));
+    h.Z = __low2half2(as_h2(q.y));
+    h.x32 = __fadd_rn(r.x, sx);
+    h.y32 = r.y;
+    h.z32 = r.z;
+    G.lo[0] = warp_min(act ? h.x32 : INFINITY);
+    G.lo[1] = warp_min(act ? h.y32 : INFINITY);
+    G.lo[2] = warp_min(act ? h.z32 : INFINITY);
+    G.hi[0] = warp_max(act ? h.x32 : -INFINITY);
+    G.hi[1] = warp_max(act ? h.y32 : -INFINITY);
+    G.hi[2] = warp_max(act ? h.z32 : -INFINITY);
+    const int mx = 1 + 2 * max(G.xm - G.xlo, G.xhi - G.xm);
+    const __half t = __float2half_rn(mx < 4 ? 0.03f : 0.06f);  // FP16 band for |X| < 4 / < 8
+    G.tau = h2_bits(__halves2half2(t, t));
+    group_rows<DIM>(S, g, cy, cz, G);
+}
+
+// All candidates of one group against its lanes; returns false when the kept
+// list needed more than one pass (the bits in S then cover only the last).
 template <int DIM, int PASS>
-__device__ __forceinline__ void walk_window(TileSmem &S, const GridDev &g, const Home &h, int wbase, int nw,
-                                            int &cnt, float &acc, bool want_rho, int *col, long long rp,
-                                            bool wc, unsigned int &n32, unsigned int &n64) {
+__device__ __forceinline__ bool run_group(TileSmem &S, const GridDev &g, Home &h, bool act, const Group &G,
+                                          float cullT, int &cnt, float &acc, int *col, long long rp,
+                                          unsigned int &n32, unsigned int &n64, int &kept_out, int p0, int nhome) {
     const int lane = threadIdx.x & 31;
-    int gi = 0;
-    unsigned int w = nw > 0 ? S.S[lane][wbase] : 0u, fin = w;
+    int cur_r = 0, cur_base = 0, passes = 0, kept = 0;
     while (true) {
-        while (w == 0u && gi < nw) {
-            S.S[lane][wbase + gi] = fin;
-            ++gi;
-            if (gi < nw) {
-                w = S.S[lane][wbase + gi];
-                fin = w;
-            }
+        kept = cull_fill<DIM>(S, g, G, cullT, cur_r, cur_base, p0, nhome);
+        ++passes;
+        const int sp = S.selfpos[lane];
+        for (int w0 = 0; w0 < kept; w0 += WIN) {
+            const int wc = min(WIN, kept - w0);
+            stage_window(S, g, w0, wc);
+            const int nwin = (wc + 31) >> 5;
+            const int self_slot = (sp >= w0 && sp < w0 + wc) ? sp - w0 : -1;
+            const unsigned int nem = test_window<DIM>(S, h, act, g.neg_t16, G.tau, w0 >> 5, nwin, self_slot);
+            walk_window<DIM, PASS>(S, g, h, w0 >> 5, nem, cnt, acc, col, rp, n32, n64);
         }
-        if (!__any_sync(0xffffffffu, gi < nw)) break;
-        if (gi < nw) {
-            const int b = __ffs(w) - 1;
-            w &= w - 1u;
-            const float4 c = S.f32[gi * 32 + b];
-            const int j = __float_as_int(c.w);
-            int in = 0;
-            float r2 = 0.f;
-            if (j != h.i) {
-                const float d0 = __fsub_rn(c.x, h.x32);
-                const float d1 = __fsub_rn(c.y, h.y32);
-                const float d2 = __fsub_rn(c.z, h.z32);
-                r2 = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
-                if (r2 < g.t32_in) {
-                    in = 1;
-                } else if (r2 > g.t32_out) {
-                    ++n32;
-                } else {
-                    ++n64;
-                    const int oi = g.orig_id[h.i], oj = g.orig_id[j];
-                    in = r2_fp64(DIM, g.xyz + (long long)oi * DIM, g.xyz + (long long)oj * DIM) < g.kh2;
-                }
-            }
-            if (in) {
-                if (want_rho) acc += g.w_norm * w_poly(sqrtf(r2) * g.r_scale);
-                if (PASS == PASS_EMIT && wc) col[rp + cnt] = j;
-                ++cnt;
-            } else {
-                fin &= ~(1u << b);
-            }
-        }
+        constexpr int NROWS = DIM == 3 ? 9 : 3;
+        if (cur_r >= NROWS) break;
     }
-    __syncwarp();
+    kept_out = kept;
+    return passes == 1;
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(32) k_nnps_tile(GridDev g, const int4 *__restrict__ tiles,
+__global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__restrict__ tiles,
                                                  const long long *__restrict__ ntiles_dev,
                                                  long long *__restrict__ row_ptr, int *__restrict__ col,
                                                  long long cap, float *__restrict__ rho,
@@ -304,9 +480,11 @@ __global__ void __launch_bounds__(32) k_nnps_tile(GridDev g, const int4 *__restr
     extern __shared__ __align__(16) unsigned char smraw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smraw);
     const int lane = threadIdx.x;
-    const int nx = g.nk[0], ny = g.nk[1];
+    const int ny = g.nk[1];
     const bool want_rho = rho != nullptr;
     const long long ntiles = *ntiles_dev;
+    // culling threshold: T plus a margin for the FP16 coordinates it uses
+    const float cullT = __half2float(__hneg(__low2half(as_h2(g.neg_t16)))) + CULL_MARGIN;
     unsigned int n32 = 0, n64 = 0;
 
     while (true) {
@@ -320,123 +498,100 @@ __global__ void __launch_bounds__(32) k_nnps_tile(GridDev g, const int4 *__restr
         const bool mine = lane < cnt_home;
         Home h;
         h.i = p0 + lane;
-        h.x = mine ? g.scell_x[h.i] : 0;
+        h.x = mine ? g.scell_x[h.i] : 0x3fffffff;
 
-        // home groups: runs of lanes whose cells span <= SPANMAX
-        int ngroups = 0;
-        {
-            int gs = 0;
-            while (gs < cnt_home) {
-                const int xa = __shfl_sync(0xffffffffu, h.x, gs);
-                const unsigned int over = __ballot_sync(0xffffffffu, mine && lane >= gs && h.x > xa + SPANMAX - 1);
-                gs = over ? __ffs(over) - 1 : cnt_home;
-                ++ngroups;
-            }
-        }
         int cnt = 0;
         float acc = 0.f;
-        const bool simple_try = ngroups == 1;
-        bool simple = simple_try;
-        // ---- pass 1 (count, or single) ---------------------------------------
-        for (int pass = 0; pass < 2; ++pass) {
-            const bool emit = pass == 1;
-            if (emit && simple) break;
-            long long rp = 0;
-            if (emit) rp = mine ? row_ptr[h.i] : 0;
-            int gs = 0;
-            while (gs < cnt_home) {
-                const int xa = __shfl_sync(0xffffffffu, h.x, gs);
-                const unsigned int over = __ballot_sync(0xffffffffu, mine && lane >= gs && h.x > xa + SPANMAX - 1);
-                const int ge = over ? __ffs(over) - 1 : cnt_home;
-                const int xb = __shfl_sync(0xffffffffu, h.x, ge - 1);
-                const bool act = mine && lane >= gs && lane < ge;
-                const int xm = (xa + xb) >> 1;
-                const int xlo = max(xa - 1, 0), xhi = min(xb + 1, nx - 1);
-                group_rows<DIM>(S, g, cy, cz, xa, xb);
-                const int C = S.C;
-                if (!emit && C > CMAX) simple = false;
-                // home frame coordinates
-                {
-                    const uint2 q = g.rel16[min(h.i, g.n - 1)];
-                    const float4 r = g.rel32[min(h.i, g.n - 1)];
-                    const float sx = 2.f * (float)(h.x - xm);
-                    const __half X = __hadd(__low2half(as_h2(q.x)), __float2half_rn(sx));
-                    h.X = __halves2half2(X, X);
-                    h.Y = __high2half2(as_h2(q.x));
-                    h.Z = __low2half2(as_h2(q.y));
-                    h.x32 = __fadd_rn(r.x, sx);
-                    h.y32 = r.y;
-                    h.z32 = r.z;
+        bool simple = true;
+        int groups = 0, kept = 0;
+        // ---- count pass (emits too when the tile is simple) ------------------
+        for (int gs = 0; gs < cnt_home;) {
+            const int xa = __shfl_sync(0xffffffffu, h.x, gs);
+            const unsigned int over = __ballot_sync(0xffffffffu, lane >= gs && h.x > xa + SPANMAX - 1);
+            const int ge = over ? __ffs(over) - 1 : cnt_home;
+            const bool act = mine && lane >= gs && lane < ge;
+            Group G;
+            group_setup<DIM>(S, g, h, act, cy, cz, gs, ge, G);
+            simple &= run_group<DIM, PASS_COUNT>(S, g, h, act, G, cullT, cnt, acc, nullptr, 0, n32, n64, kept, p0,
+                                                 cnt_home);
+            ++groups;
+            gs = ge;
+        }
+        simple &= groups == 1;
+        // ---- CSR offset of the tile --------------------------------------------
+        int inc = mine ? cnt : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int agg = __shfl_sync(0xffffffffu, inc, 31);
+        const long long rstart = inc - (mine ? cnt : 0);
+        const long long pre = look_back(tstate, t, agg, &g.status->flags);
+        const bool wc = col != nullptr && pre + agg <= cap;
+        if (col != nullptr && !wc && lane == 0) atomicOr(&g.status->flags, ST_CAPACITY);
+        if (mine) {
+            row_ptr[h.i] = pre + rstart;
+            if (want_rho) rho[h.i] = g.w_norm * (2.f / 3.f + acc);
+        }
+        if (t == ntiles - 1 && lane == 0) row_ptr[g.n] = pre + agg;
+        if (!wc) continue;
+        if (simple) {
+            // emit the row from the kept bits of the single pass: each lane
+            // writes its row's candidate slots into a 16-bit staging area
+            // (the window buffers, free now), then the warp copies the tile's
+            // columns out with consecutive lanes on consecutive entries
+            const int nw = mine ? (kept + 31) >> 5 : 0;
+            const bool staged = agg <= STG_SLOTS;
+            unsigned short *stg = reinterpret_cast<unsigned short *>(&S.pw[0]);
+            long long pos = staged ? rstart : pre + rstart;
+            unsigned int nem = 0;
+            for (int q = 0; q < nw; ++q) nem |= (S.S[lane][q] != 0u ? 1u : 0u) << q;
+            int gi = 0;
+            unsigned int w = 0u;
+            constexpr int EB = 8;
+            while (true) {
+                int p[EB];
+                bool v[EB];
+                next_bits<EB>(S, lane, 0, nem, gi, w, p, v);
+                if (!__any_sync(0xffffffffu, v[0])) break;
+                if (staged) {
+#pragma unroll
+                    for (int k = 0; k < EB; ++k)
+                        if (v[k]) stg[pos + k] = (unsigned short)p[k];
+                } else {
+                    int jv[EB];
+#pragma unroll
+                    for (int k = 0; k < EB; ++k) jv[k] = S.jall[v[k] ? p[k] : 0];
+#pragma unroll
+                    for (int k = 0; k < EB; ++k)
+                        if (v[k]) col[pos + k] = jv[k];
                 }
-                const int mx = 1 + 2 * max(xm - xlo, xhi - xm);
-                const unsigned int tau = tau16_bits(mx);
-                for (int s0 = 0; s0 < C; s0 += CMAX) {
-                    const int sc = min(CMAX, C - s0);
-                    for (int w0 = s0; w0 < s0 + sc; w0 += WIN) {
-                        const int wc = min(WIN, s0 + sc - w0);
-                        stage_window(S, g, w0, wc, s0, xlo, xm);
-                        const int wbase = (w0 - s0) >> 5;
-                        test_window<DIM>(S, h, act, g.neg_t16, tau, wbase);
-                        const int nw = (wc + 31) >> 5;
-                        if (emit)
-                            walk_window<DIM, PASS_EMIT>(S, g, h, wbase, act ? nw : 0, cnt, acc, false, col, rp,
-                                                        true, n32, n64);
-                        else
-                            walk_window<DIM, PASS_COUNT>(S, g, h, wbase, act ? nw : 0, cnt, acc, want_rho,
-                                                         nullptr, 0, false, n32, n64);
-                    }
-                }
-                gs = ge;
+#pragma unroll
+                for (int k = 0; k < EB; ++k) pos += v[k] ? 1 : 0;
             }
-            if (!emit) {
-                // ---- offsets across tiles --------------------------------------
-                int inc = mine ? cnt : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += v;
-                }
-                const int agg = __shfl_sync(0xffffffffu, inc, 31);
-                const int roff = inc - (mine ? cnt : 0);
-                const long long pre = look_back(tstate, t, agg, &g.status->flags);
-                const bool wc = col != nullptr && pre + agg <= cap;
-                if (col != nullptr && !wc && lane == 0) atomicOr(&g.status->flags, ST_CAPACITY);
-                if (mine) {
-                    row_ptr[h.i] = pre + roff;
-                    if (want_rho) rho[h.i] = g.w_self + acc;
-                }
-                if (t == ntiles - 1 && lane == 0) row_ptr[g.n] = pre + agg;
-                if (simple && wc && col != nullptr) {
-                    // emit each row from its kept bits; the column index comes
-                    // from the candidate row table (rows are contiguous ranges)
-                    const int nw = (S.C + 31) >> 5;
-                    long long pos = pre + roff;
-                    int gi = 0;
-                    unsigned int w = (mine && nw > 0) ? S.S[lane][0] : 0u;
-                    while (true) {
-                        while (w == 0u && gi < nw) {
-                            ++gi;
-                            if (gi < nw) w = mine ? S.S[lane][gi] : 0u;
-                        }
-                        if (!__any_sync(0xffffffffu, gi < nw)) break;
-                        if (gi < nw) {
-                            const int b = __ffs(w) - 1;
-                            w &= w - 1u;
-                            const int p = gi * 32 + b;
-                            int r = 0;
-#pragma unroll
-                            for (int q = 1; q < 9; ++q) r = (p >= S.roff[q]) ? q : r;
-                            col[pos++] = S.rstart[r] + (p - S.roff[r]);
-                        }
-                    }
-                    __syncwarp();
-                }
-                if (!simple) {
-                    // second pass re-derives the rows and writes them in place
-                    cnt = 0;
-                    acc = 0.f;
-                    if (!wc) break;
-                }
+            __syncwarp();
+            if (staged) {
+#pragma unroll 4
+                for (int e = lane; e < agg; e += 32) col[pre + e] = S.jall[stg[e]];
+                __syncwarp();
+            }
+        } else {
+            // emit pass: same decisions again, written straight to the rows
+            int ecnt = 0;
+            float dummy = 0.f;
+            unsigned int e32 = 0, e64 = 0;
+            for (int gs = 0; gs < cnt_home;) {
+                const int xa = __shfl_sync(0xffffffffu, h.x, gs);
+                const unsigned int over = __ballot_sync(0xffffffffu, lane >= gs && h.x > xa + SPANMAX - 1);
+                const int ge = over ? __ffs(over) - 1 : cnt_home;
+                const bool act = mine && lane >= gs && lane < ge;
+                Group G;
+                group_setup<DIM>(S, g, h, act, cy, cz, gs, ge, G);
+                int kk;
+                run_group<DIM, PASS_EMIT>(S, g, h, act, G, cullT, ecnt, dummy, col, pre + rstart, e32, e64, kk, p0,
+                                          cnt_home);
+                gs = ge;
             }
         }
     }

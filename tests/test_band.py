@@ -119,6 +119,42 @@ def test_fp32_band_sound(dim, T):
     assert np.all(np.abs(D2[undecided] - T) < 2 * tau32 + 5e-6)
 
 
+def fp16_e_frame(ai, aj, oi, oj, T):
+    """Row-tile arithmetic: both coordinates re-expressed in a frame cell,
+    X = fl16(q + 2 o) with integer cell offsets o, then the same e chain."""
+    f16 = lambda x: np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+    Xi = f16(f16(ai) + 2.0 * oi)
+    Xj = f16(f16(aj) + 2.0 * oj)
+    d = f16(Xj - Xi)
+    e = f16(d[:, 0] * d[:, 0] - float(t16_up(T)))
+    for k in range(1, ai.shape[1]):
+        e = f16(d[:, k] * d[:, k] + e)
+    return e
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("maxoff,tau", [(1, 0.03), (3, 0.06)])
+def test_fp16_band_sound_in_tile_frame(dim, maxoff, tau):
+    """Frame coordinates with x cell offsets up to +-maxoff (|X| < 4 for 1,
+    |X| < 8 for 3): every true neighbour keeps e below the band the tile
+    search uses for that magnitude."""
+    T = 4.0 * (1 - 2.0 ** -29)
+    ai, aj, sh = pairs_near_threshold(1_500_000, dim, T, width=0.1)
+    oi = np.zeros_like(ai)
+    oi[:, 0] = RNG.integers(-maxoff + 1, maxoff, size=ai.shape[0]) if maxoff > 1 else 0
+    oj = oi + sh
+    ok = np.abs(oj[:, 0]) <= maxoff
+    if dim == 3:
+        ok &= np.all(np.abs(oj[:, 1:]) <= 1, axis=1)
+    ai, aj, oi, oj, sh = ai[ok], aj[ok], oi[ok], oj[ok], sh[ok]
+    D2 = np.sum((aj + 2.0 * sh - ai) ** 2, axis=1)
+    e = fp16_e_frame(ai, aj, oi, oj, T)
+    nb = D2 < T
+    assert nb.sum() > 1000
+    assert np.all(e[nb] < tau)
+    assert float((e - (D2 - T))[np.abs(D2 - T) < 0.5].max()) <= (0.0199 if maxoff == 1 else 0.044)
+
+
 def test_fp16_band_is_needed():
     """Without the band the FP16 test would lose true neighbours (so the test
     above is not vacuous)."""
