@@ -35,7 +35,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["3d_1m", "2d_10k", "3d_8m"], default="3d_1m")
@@ -81,7 +81,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("nnps.cu", "sph_internal.cuh"):
+    for name in ("nnps_tile.cu", "nnps_common.cuh", "sph_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2401_08586_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -119,7 +119,11 @@ class ClockSampler:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            # the timed region starts only once the sampler is producing rows
+            t_end = time.time() + 10.0
+            while time.time() < t_end and os.path.getsize(self.tmp.name) == 0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -305,7 +309,7 @@ def main():
     alg_dom = n * (8 + 16 + 8 + 4) + 4 * nnz
     peak, peak_src = measured_peaks()
     achieved = alg_dom / (dom_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_nnps_fused" if dom == "fused" else "k_nnps<fill>",
+    roofline = {"bound": "hbm", "kernel": "k_nnps_tile" if dom == "fused" else "k_nnps<fill>",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "launch_ms": dom_ms, "algorithmic_bytes_per_launch": alg_dom,
                 "traffic": ncu_traffic(args.workload, dom)}
