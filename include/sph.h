@@ -255,8 +255,13 @@ int sph_grid_csr(sph_grid_t grid, const int64_t **row_ptr, const int32_t **col, 
  * sph_profile_read waits for the recorded events and returns the summed
  * milliseconds and launch count for one kernel tag since the last reset:
  * "bounds", "hash", "scan", "scatter", "sort", "convert", "count", "fill",
- * "density", "canon". */
+ * "density", "canon", "fused", "batch", "step".
+ * sph_profile_select enables the events for the listed tags only
+ * (comma-separated, e.g. "fused"; NULL: all), so that a timed loop pays for
+ * events around the kernels it reports and no others.  SPH_ERR_INVALID for an
+ * unknown tag (the selection is then unchanged). */
 int sph_profile_enable(int on);
+int sph_profile_select(const char *kernels);
 int sph_profile_reset(void);
 int sph_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 

@@ -17,7 +17,8 @@ cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st
                           cudaStream_t s);
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec,
                                         int *cnt, int *cid, int *slot, int *cell_start, int *orig_id,
-                                        int *rank, int *scell, uint2 *rel16, float4 *rel32, double4 *x64,
+                                        int *rank, int *scell, uint2 *rel16, float4 *rel32, uint2 *rel16u,
+                                        float4 *rel32u, double4 *x64,
                                         void *scan_tmp, int *big_list, unsigned int *big_count,
                                         int check_box, int sm_count, cudaStream_t s);
 cudaError_t launch_nnps(const GridDev &g, int prec, int mode_fill, int *cnt, const long long *row_ptr,
@@ -86,7 +87,7 @@ struct sph_grid_s {
     double lo[3] = {0, 0, 0};
     double hc = 0;
     const double *xyz = nullptr;
-    DevBuf cell_start, cnt, cid, slot, orig_id, rank, scell, rel16, rel32, x64, scan_tmp, big_list,
+    DevBuf cell_start, cnt, cid, slot, orig_id, rank, scell, rel16, rel32, rel16u, rel32u, x64, scan_tmp, big_list,
         rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho, tstate, scell_x, tcount,
         toff, tiles;
     int fused_enabled = 1;  // search variant for cell-order FP16 queries (SPH_OPT_FUSED)
@@ -357,7 +358,8 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
             (rc = ensure(g->big_list, big * sizeof(int), s)))
             break;
         if (p->precision == SPH_PREC_FP16_RCLL) {
-            if ((rc = ensure(g->rel16, nn * sizeof(uint2), s)) || (rc = ensure(g->rel32, nn * sizeof(float4), s)))
+            if ((rc = ensure(g->rel16, nn * sizeof(uint2), s)) || (rc = ensure(g->rel32, nn * sizeof(float4), s)) ||
+                (rc = ensure(g->rel16u, nn * sizeof(uint2), s)) || (rc = ensure(g->rel32u, nn * sizeof(float4), s)))
                 break;
         } else {
             if ((rc = ensure(g->x64, nn * sizeof(double4), s))) break;
@@ -373,7 +375,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
         cudaError_t e = launch_hash_scatter_convert(
             d, xyz, (int)n, dim, p->precision, P<int>(g->cnt), P<int>(g->cid), P<int>(g->slot),
             P<int>(g->cell_start), P<int>(g->orig_id), P<int>(g->rank), P<int>(g->scell), P<uint2>(g->rel16),
-            P<float4>(g->rel32), P<double4>(g->x64), g->scan_tmp.p, P<int>(g->big_list),
+            P<float4>(g->rel32), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4>(g->x64), g->scan_tmp.p, P<int>(g->big_list),
             &P<DevStatus>(g->status)->big_cells, p->have_box, g->sm_count, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -610,6 +612,11 @@ extern "C" int sph_profile_enable(int on) {
     return SPH_OK;
 }
 
+extern "C" int sph_profile_select(const char *kernels) {
+    if (prof_select(kernels) != 0) return fail(SPH_ERR_INVALID, "unknown kernel tag in \"%s\"", kernels);
+    return SPH_OK;
+}
+
 extern "C" int sph_profile_reset(void) {
     prof_reset();
     return SPH_OK;
@@ -654,8 +661,8 @@ extern "C" int sph_grid_free(sph_grid_t grid) {
     if (!g) return SPH_OK;
     cudaStream_t s = g->stream;
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
-                      &g->rel16, &g->rel32, &g->x64, &g->scan_tmp, &g->big_list, &g->rowcnt, &g->tmp_rp,
-                      &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
+                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->x64, &g->scan_tmp, &g->big_list,
+                      &g->rowcnt, &g->tmp_rp, &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
                       &g->tstate, &g->scell_x, &g->tcount, &g->toff, &g->tiles};
     for (DevBuf *b : bufs) release(*b, s);
     if (g->h_status) {

@@ -5,49 +5,79 @@
 // Steps (one pass each over the particles):
 //   k_bounds   per-axis min/max of the FP64 coordinates (Eq. 5 uses the
 //              domain extent), finiteness check;
-//   k_hash     cell index c_k = clamp(floor((x_k - lo_k) / h_c), 0, n_k - 1),
-//              linear id (c_z n_y + c_y) n_x + c_x, warp-aggregated histogram
-//              whose returned counter value is the particle's provisional slot;
+//   k_hash     cell index c_k = clamp(floor((x_k - lo_k) / h_c), 0, n_k - 1)
+//              and the relative coordinate x_rel = 2 (x - x_cc) / h_c with
+//              x_cc the cell centre, computed in FP64 and rounded once to FP16
+//              and FP32 (input order); linear id (c_z n_y + c_y) n_x + c_x,
+//              warp-aggregated histogram whose returned counter value is the
+//              particle's provisional slot;
 //   (exclusive scan of the histogram -> cell_start)
 //   k_scatter  orig_id[cell_start[cell] + slot] = i;
 //   (per-cell sort of orig_id, so the order inside a cell is the input order
 //    and the result does not depend on atomic timing)
-//   k_convert  for every sorted position: rank, cell id, and the relative
-//              coordinate x_rel = 2 (x - x_cc) / h_c with x_cc the cell centre,
-//              computed in FP64 and rounded once to FP16 (rel16) and FP32
-//              (rel32); or, for the FP64 cell link-list, the FP64 coordinate.
+//   k_convert  for every sorted position: rank, cell id and the relative
+//              coordinates gathered into cell order (rel16, rel32); or, for
+//              the FP64 cell link-list, the FP64 coordinate.
+// The FP64 work is one pass of five operations per axis: this part's FP64
+// rate is a small fraction of its FP32 and integer rates.
 #include "profile.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
 
-__global__ void k_bounds(const double *__restrict__ xyz, long long total, int dim,
-                         DevStatus *st) {
-    // Launched with a thread count that is a multiple of dim, so each thread
-    // always reads the same axis.
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    const int axis = (int)(t % dim);
-    double mn = INFINITY, mx = -INFINITY;
+// Order-preserving integer key of an FP64 value (same map as dkey).
+__device__ __forceinline__ unsigned long long key_of(unsigned long long b) {
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ void key_minmax(unsigned long long b, unsigned long long &mn, unsigned long long &mx,
+                                           bool &bad) {
+    bad |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+    const unsigned long long k = key_of(b);
+    mn = k < mn ? k : mn;
+    mx = k > mx ? k : mx;
+}
+
+// Per-axis min/max over the order-preserving integer keys of the FP64
+// coordinates (no FP64 arithmetic: this part's FP64 rate is a small fraction
+// of its integer rate), and the finiteness check on the exponent bits.
+// Each thread step reads six consecutive values as three 16-byte loads
+// (six is a multiple of both dimensions, so value j of a step is on axis
+// j % dim); a misaligned array or the tail goes value by value.
+__global__ void k_bounds(const double *__restrict__ xyz, long long total, int dim, DevStatus *st) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned long long *bits = reinterpret_cast<const unsigned long long *>(xyz);
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
     bool bad = false;
-    for (long long f = t; f < total; f += stride) {
-        double x = xyz[f];
-        bad |= !isfinite(x);
-        mn = fmin(mn, x);
-        mx = fmax(mx, x);
+    const bool aligned = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
+    const long long nchunk = aligned ? total / 6 : 0;
+    const ulonglong2 *v2 = reinterpret_cast<const ulonglong2 *>(xyz);
+    for (long long c = t; c < nchunk; c += stride) {
+        const ulonglong2 a = __ldg(v2 + 3 * c), b = __ldg(v2 + 3 * c + 1), d = __ldg(v2 + 3 * c + 2);
+        const unsigned long long e[6] = {a.x, a.y, b.x, b.y, d.x, d.y};
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const int ax = j % 3;
+            if (dim == 3) key_minmax(e[j], mn[ax], mx[ax], bad);
+            else key_minmax(e[j], mn[j & 1], mx[j & 1], bad);
+        }
     }
-    if (bad) atomicOr(&st->flags, ST_NONFINITE);
-    // Reduce lanes that read the same axis: with 32 lanes and dim in {2,3} the
-    // lanes of one axis are lane = axis0 + k*dim; simplest is a shared-memory
-    // reduction per axis.
-    __shared__ double smin[3][32], smax[3][32];
+    for (long long f = nchunk * 6 + t; f < total; f += stride) {
+        const int ax = (int)(f % dim);
+        key_minmax(__ldg(bits + f), mn[ax], mx[ax], bad);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->flags, ST_NONFINITE);
+    __shared__ unsigned long long smin[3][32], smax[3][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int a = 0; a < 3; ++a) {
-        double vmn = (axis == a) ? mn : INFINITY;
-        double vmx = (axis == a) ? mx : -INFINITY;
+    for (int a = 0; a < dim; ++a) {
+        unsigned long long vmn = mn[a], vmx = mx[a];
+#pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            vmn = fmin(vmn, __shfl_xor_sync(0xffffffffu, vmn, o));
-            vmx = fmax(vmx, __shfl_xor_sync(0xffffffffu, vmx, o));
+            const unsigned long long pm = __shfl_xor_sync(0xffffffffu, vmn, o);
+            const unsigned long long px = __shfl_xor_sync(0xffffffffu, vmx, o);
+            vmn = pm < vmn ? pm : vmn;
+            vmx = px > vmx ? px : vmx;
         }
         if (lane == 0) {
             smin[a][w] = vmn;
@@ -56,21 +86,40 @@ __global__ void k_bounds(const double *__restrict__ xyz, long long total, int di
     }
     __syncthreads();
     if (threadIdx.x < dim) {
-        int a = threadIdx.x;
-        double vmn = INFINITY, vmx = -INFINITY;
+        const int a = threadIdx.x;
+        unsigned long long vmn = ~0ull, vmx = 0ull;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            vmn = fmin(vmn, smin[a][k]);
-            vmx = fmax(vmx, smax[a][k]);
+            vmn = smin[a][k] < vmn ? smin[a][k] : vmn;
+            vmx = smax[a][k] > vmx ? smax[a][k] : vmx;
         }
         if (vmn <= vmx) {
-            atomicMin(&st->min_key[a], dkey(vmn));
-            atomicMax(&st->max_key[a], dkey(vmx));
+            atomicMin(&st->min_key[a], vmn);
+            atomicMax(&st->max_key[a], vmx);
         }
     }
 }
 
+// Cell index and cell-relative coordinate of one axis, in units of
+// u = h_c / 2 (Eq. 6 with the cell centre as reference):
+//   s = 2 (x - lo) / h_c,  c = clamp(floor(s / 2), 0, nk - 1),
+//   a = s - (2c + 1)  (exact: s and 2c + 1 are within one of each other).
+// Five FP64 operations and no division.  s carries a relative error of at
+// most 2^-52 (x - lo is exact whenever x and lo are within a factor of two),
+// i.e. at most 2^-31 u at the 2^20-cell limit, below the 2^-29 u margin that
+// the cell size kh (1 + 2^-30) leaves, so every pair closer than kh sits in
+// the same or adjacent cells.
+__device__ __forceinline__ int rel_axis(double x, double lo, double two_over_hc, int nk, double &a) {
+    const double s = __dmul_rn(__dsub_rn(x, lo), two_over_hc);
+    int c = __double2int_rd(s) >> 1;  // floor(floor(s) / 2) = floor(s / 2); saturating conversion
+    c = min(max(c, 0), nk - 1);
+    a = __dsub_rn(s, (double)(2 * c + 1));
+    return c;
+}
+
+template <int PREC>
 __global__ void k_hash(const double *__restrict__ xyz, int n, int dim, GridDev g,
-                       int *__restrict__ cnt, int *__restrict__ cid, int *__restrict__ slot) {
+                       int *__restrict__ cnt, int *__restrict__ cid, int *__restrict__ slot,
+                       uint2 *__restrict__ rel16u, float4 *__restrict__ rel32u, int check_box) {
     const int lane = threadIdx.x & 31;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
          base += (long long)gridDim.x * blockDim.x) {
@@ -79,9 +128,25 @@ __global__ void k_hash(const double *__restrict__ xyz, int n, int dim, GridDev g
         int c = -1;
         if (live) {
             int cc[3] = {0, 0, 0};
-            for (int k = 0; k < dim; ++k)
-                cc[k] = cell_coord(xyz[i * dim + k], g.lo[k], g.hc, g.nk[k]);
+            double a[3] = {0.0, 0.0, 0.0};
+            bool out = false;
+            for (int k = 0; k < dim; ++k) {
+                cc[k] = rel_axis(xyz[i * dim + k], g.lo[k], g.two_over_hc, g.nk[k], a[k]);
+                out |= fabs(a[k]) > 1.0 + 1e-6;
+            }
+            if (out && check_box) atomicOr(&g.status->flags, ST_OUT_OF_BOX);
             c = (cc[2] * g.nk[1] + cc[1]) * g.nk[0] + cc[0];
+            if (PREC == SPH_PREC_FP16_RCLL) {
+                // rounded once, to nearest even, from the FP64 value
+                const __half2 xy = __halves2half2(__double2half(a[0]), __double2half(a[1]));
+                const __half2 z0 = __halves2half2(__double2half(a[2]), __double2half(0.0));
+                uint2 q;
+                q.x = *reinterpret_cast<const unsigned int *>(&xy);
+                q.y = *reinterpret_cast<const unsigned int *>(&z0);
+                rel16u[i] = q;
+                rel32u[i] = make_float4(__double2float_rn(a[0]), __double2float_rn(a[1]),
+                                        __double2float_rn(a[2]), 0.f);
+            }
         }
         // Lanes with the same cell add to its counter once.
         unsigned int peers = __match_any_sync(0xffffffffu, c);
@@ -103,46 +168,27 @@ __global__ void k_scatter(int n, const int *__restrict__ cell_start, const int *
         orig_id[cell_start[cid[i]] + slot[i]] = (int)i;
 }
 
+// Sorted position s takes input particle i = orig_id[s]: its rank, cell and
+// (RCLL) the relative coordinates computed by k_hash, or (FP64 cell
+// link-list) its FP64 coordinates.
 template <int PREC>
 __global__ void k_convert(int n, int dim, GridDev g, const int *__restrict__ cid_in,
                           int *__restrict__ rank, int *__restrict__ scell, uint2 *__restrict__ rel16,
-                          float4 *__restrict__ rel32, double4 *__restrict__ x64, int check_box) {
+                          float4 *__restrict__ rel32, const uint2 *__restrict__ rel16u,
+                          const float4 *__restrict__ rel32u, double4 *__restrict__ x64) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
-        int i = g.orig_id[s];
+        const int i = g.orig_id[s];
         rank[i] = (int)s;
         scell[s] = cid_in[i];
-        double x[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];
         if (PREC == SPH_PREC_FP64_CLL) {
+            double x[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];
             x64[s] = make_double4(x[0], x[1], x[2], 0.0);
-            if (check_box) {
-                for (int k = 0; k < dim; ++k)
-                    if (x[k] < g.lo[k] || x[k] > g.lo[k] + g.nk[k] * g.hc)
-                        atomicOr(&g.status->flags, ST_OUT_OF_BOX);
-            }
-            continue;
+        } else {
+            rel16[s] = rel16u[i];
+            rel32[s] = rel32u[i];
         }
-        double a[3] = {0.0, 0.0, 0.0};
-        bool out = false;
-        for (int k = 0; k < dim; ++k) {
-            int c = cell_coord(x[k], g.lo[k], g.hc, g.nk[k]);
-            // x - x_cc with x_cc = lo + (c + 1/2) h_c: one rounding for the
-            // difference to lo, one for the fused subtraction of the centre.
-            double t = __dsub_rn(x[k], g.lo[k]);
-            double r = __fma_rn(-((double)c + 0.5), g.hc, t);
-            a[k] = __dmul_rn(r, g.two_over_hc);
-            out |= fabs(a[k]) > 1.0 + 1e-6;
-        }
-        if (out && check_box) atomicOr(&g.status->flags, ST_OUT_OF_BOX);
-        __half2 xy = __halves2half2(__double2half(a[0]), __double2half(a[1]));
-        __half2 z0 = __halves2half2(__double2half(a[2]), __double2half(0.0));
-        uint2 q;
-        q.x = *reinterpret_cast<unsigned int *>(&xy);
-        q.y = *reinterpret_cast<unsigned int *>(&z0);
-        rel16[s] = q;
-        rel32[s] = make_float4(__double2float_rn(a[0]), __double2float_rn(a[1]),
-                               __double2float_rn(a[2]), 0.f);
     }
 }
 
@@ -156,18 +202,18 @@ static unsigned grid_for(long long n, int nt, int sm_count, int per_sm) {
 
 cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count,
                           cudaStream_t s) {
-    const int nt = 192;  // multiple of 2 and 3: each thread keeps one axis
+    const int nt = 256;
     ProfScope ps(TAG_BOUNDS, s);
     note_launch(1);
-    k_bounds<<<grid_for(n * dim, nt, sm_count, 8), nt, 0, s>>>(xyz, n * dim, dim, st);
+    k_bounds<<<grid_for((n * dim + 5) / 6, nt, sm_count, 8), nt, 0, s>>>(xyz, n * dim, dim, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec,
                                         int *cnt, int *cid, int *slot, int *cell_start, int *orig_id,
-                                        int *rank, int *scell, uint2 *rel16, float4 *rel32, double4 *x64,
-                                        void *scan_tmp, int *big_list, unsigned int *big_count,
-                                        int check_box, int sm_count, cudaStream_t s) {
+                                        int *rank, int *scell, uint2 *rel16, float4 *rel32, uint2 *rel16u,
+                                        float4 *rel32u, double4 *x64, void *scan_tmp, int *big_list,
+                                        unsigned int *big_count, int check_box, int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
     cudaError_t e = cudaMemsetAsync(cnt, 0, g.ncell * sizeof(int), s);
@@ -175,7 +221,12 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
     {
         ProfScope ps(TAG_HASH, s);
         note_launch(1);
-        k_hash<<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot);
+        if (prec == SPH_PREC_FP16_RCLL)
+            k_hash<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot, rel16u, rel32u,
+                                                             check_box);
+        else
+            k_hash<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot, nullptr, nullptr,
+                                                            check_box);
     }
     e = exclusive_scan_i32(cnt, cell_start, g.ncell, scan_tmp, s);
     if (e != cudaSuccess) return e;
@@ -190,10 +241,10 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
     note_launch(1);
     if (prec == SPH_PREC_FP16_RCLL)
         k_convert<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, rel16, rel32,
-                                                            nullptr, check_box);
+                                                            rel16u, rel32u, nullptr);
     else
         k_convert<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, nullptr, nullptr,
-                                                           x64, check_box);
+                                                           nullptr, nullptr, x64);
     return cudaGetLastError();
 }
 

@@ -81,15 +81,22 @@ __device__ __forceinline__ float w_poly_bf(float R) {
     return R < 1.f ? w1 : w2;
 }
 
-// Publish this tile's total and return the sum over all earlier tiles.
-__device__ __forceinline__ long long look_back(unsigned long long *tstate, long long t, long long agg,
-                                               unsigned int *flags) {
+// Publish this tile's total (an aggregate, or already the inclusive prefix
+// for tile 0).  Successors can use it before this tile has resolved its own
+// prefix.
+__device__ __forceinline__ void look_back_publish(unsigned long long *tstate, long long t, long long agg) {
+    if ((threadIdx.x & 31) == 0)
+        atomicExch(&tstate[t], (t == 0 ? ST_INCL : ST_AGG) | (unsigned long long)agg);
+}
+
+// Sum of all earlier tiles' totals, by looking back over their published
+// states 32 at a time (stopping at the first inclusive prefix); then publish
+// this tile's inclusive prefix.  Every wait is bounded: after
+// LOOKBACK_SPIN_LIMIT polls the tile records ST_TIMEOUT and continues.
+__device__ __forceinline__ long long look_back_resolve(unsigned long long *tstate, long long t, long long agg,
+                                                       unsigned int *flags) {
     const int lane = threadIdx.x & 31;
-    if (t == 0) {
-        if (lane == 0) atomicExch(&tstate[0], ST_INCL | (unsigned long long)agg);
-        return 0;
-    }
-    if (lane == 0) atomicExch(&tstate[t], ST_AGG | (unsigned long long)agg);
+    if (t == 0) return 0;
     long long excl = 0, j = t - 1;
     int spins = 0, backoff = 32;
     bool timed_out = false;
@@ -471,6 +478,39 @@ __device__ __forceinline__ bool run_group(TileSmem &S, const GridDev &g, Home &h
     return passes == 1;
 }
 
+// Emit the lane's kept bits (words [0, nw) of its row) in order: candidate
+// slots as 16-bit entries to stg[pos...], or (stg == nullptr) the sorted
+// indices jall[slot] to col[pos...].
+__device__ __forceinline__ void emit_bits(const TileSmem &S, int lane, int nw, long long pos, unsigned short *stg,
+                                          int *col, const int *jall) {
+    unsigned int nem = 0;
+    for (int q = 0; q < nw; ++q) nem |= (S.S[lane][q] != 0u ? 1u : 0u) << q;
+    int gi = 0;
+    unsigned int w = 0u;
+    constexpr int EB = 8;
+    while (true) {
+        int p[EB];
+        bool v[EB];
+        next_bits<EB>(S, lane, 0, nem, gi, w, p, v);
+        if (!__any_sync(0xffffffffu, v[0])) break;
+        if (stg != nullptr) {
+#pragma unroll
+            for (int k = 0; k < EB; ++k)
+                if (v[k]) stg[pos + k] = (unsigned short)p[k];
+        } else {
+            int jv[EB];
+#pragma unroll
+            for (int k = 0; k < EB; ++k) jv[k] = jall[v[k] ? p[k] : 0];
+#pragma unroll
+            for (int k = 0; k < EB; ++k)
+                if (v[k]) col[pos + k] = jv[k];
+        }
+#pragma unroll
+        for (int k = 0; k < EB; ++k) pos += v[k] ? 1 : 0;
+    }
+    __syncwarp();
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__restrict__ tiles,
                                                  const long long *__restrict__ ntiles_dev,
@@ -527,7 +567,14 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__r
         }
         const int agg = __shfl_sync(0xffffffffu, inc, 31);
         const long long rstart = inc - (mine ? cnt : 0);
-        const long long pre = look_back(tstate, t, agg, &g.status->flags);
+        look_back_publish(tstate, t, agg);
+        // A simple tile whose row segment fits the staging area lays its
+        // output out in shared memory before it needs its CSR offset, so the
+        // wait on earlier tiles overlaps that work.
+        const bool staged = simple && col != nullptr && agg <= STG_SLOTS;
+        unsigned short *stg = reinterpret_cast<unsigned short *>(&S.pw[0]);
+        if (staged) emit_bits(S, lane, mine ? (kept + 31) >> 5 : 0, rstart, stg, nullptr, nullptr);
+        const long long pre = look_back_resolve(tstate, t, agg, &g.status->flags);
         const bool wc = col != nullptr && pre + agg <= cap;
         if (col != nullptr && !wc && lane == 0) atomicOr(&g.status->flags, ST_CAPACITY);
         if (mine) {
@@ -536,46 +583,14 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__r
         }
         if (t == ntiles - 1 && lane == 0) row_ptr[g.n] = pre + agg;
         if (!wc) continue;
-        if (simple) {
-            // emit the row from the kept bits of the single pass: each lane
-            // writes its row's candidate slots into a 16-bit staging area
-            // (the window buffers, free now), then the warp copies the tile's
-            // columns out with consecutive lanes on consecutive entries
-            const int nw = mine ? (kept + 31) >> 5 : 0;
-            const bool staged = agg <= STG_SLOTS;
-            unsigned short *stg = reinterpret_cast<unsigned short *>(&S.pw[0]);
-            long long pos = staged ? rstart : pre + rstart;
-            unsigned int nem = 0;
-            for (int q = 0; q < nw; ++q) nem |= (S.S[lane][q] != 0u ? 1u : 0u) << q;
-            int gi = 0;
-            unsigned int w = 0u;
-            constexpr int EB = 8;
-            while (true) {
-                int p[EB];
-                bool v[EB];
-                next_bits<EB>(S, lane, 0, nem, gi, w, p, v);
-                if (!__any_sync(0xffffffffu, v[0])) break;
-                if (staged) {
-#pragma unroll
-                    for (int k = 0; k < EB; ++k)
-                        if (v[k]) stg[pos + k] = (unsigned short)p[k];
-                } else {
-                    int jv[EB];
-#pragma unroll
-                    for (int k = 0; k < EB; ++k) jv[k] = S.jall[v[k] ? p[k] : 0];
-#pragma unroll
-                    for (int k = 0; k < EB; ++k)
-                        if (v[k]) col[pos + k] = jv[k];
-                }
-#pragma unroll
-                for (int k = 0; k < EB; ++k) pos += v[k] ? 1 : 0;
-            }
-            __syncwarp();
-            if (staged) {
+        if (staged) {
+            // consecutive lanes on consecutive entries of the tile's segment
 #pragma unroll 4
-                for (int e = lane; e < agg; e += 32) col[pre + e] = S.jall[stg[e]];
-                __syncwarp();
-            }
+            for (int e = lane; e < agg; e += 32) col[pre + e] = S.jall[stg[e]];
+            __syncwarp();
+        } else if (simple) {
+            // segment larger than the staging area: rows straight to col
+            emit_bits(S, lane, mine ? (kept + 31) >> 5 : 0, pre + rstart, nullptr, col, S.jall);
         } else {
             // emit pass: same decisions again, written straight to the rows
             int ecnt = 0;

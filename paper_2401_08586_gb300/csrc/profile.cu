@@ -45,7 +45,7 @@ static cudaEvent_t take_event() {
 }
 
 ProfScope::ProfScope(int tag, cudaStream_t s) : tag_(tag), s_(s), a_(nullptr) {
-    if (!g_enabled.load(std::memory_order_relaxed)) return;
+    if (!((g_enabled.load(std::memory_order_relaxed) >> tag) & 1)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = take_event();
     cudaEventRecord((cudaEvent_t)a_, s_);
@@ -75,7 +75,30 @@ static void drain_locked() {
 
 void prof_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_enabled.store(on ? 1 : 0);
+    g_enabled.store(on ? (1 << TAG_COUNT_) - 1 : 0);
+}
+
+int prof_select(const char *names) {
+    if (names == nullptr) {
+        prof_enable(1);
+        return 0;
+    }
+    int mask = 0;
+    const char *p = names;
+    while (*p) {
+        const char *e = strchr(p, ',');
+        const size_t len = e ? (size_t)(e - p) : strlen(p);
+        int found = -1;
+        for (int t = 0; t < TAG_COUNT_; ++t)
+            if (strlen(g_names[t]) == len && strncmp(p, g_names[t], len) == 0) found = t;
+        if (found < 0) return -1;
+        mask |= 1 << found;
+        p += len;
+        if (*p == ',') ++p;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_enabled.store(mask);
+    return 0;
 }
 
 void prof_reset() {

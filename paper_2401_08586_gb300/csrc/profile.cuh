@@ -42,6 +42,9 @@ class ProfScope {
 };
 
 void prof_enable(int on);
+// Enable timing for a comma-separated list of tag names only (NULL: all);
+// -1 if a name is unknown (nothing changed).
+int prof_select(const char *names);
 void prof_reset();
 int prof_read(const char *name, double *ms, long long *calls);
 

@@ -91,6 +91,7 @@ def load(build_if_missing=False):
                          ctypes.POINTER(ctypes.c_int64)],
         "sph_profile_enable": [ctypes.c_int],
         "sph_profile_reset": [],
+        "sph_profile_select": [ctypes.c_char_p],
         "sph_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "sph_launch_count": [],
         "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
@@ -110,8 +111,8 @@ def exported_symbols():
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
             "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
-            "sph_profile_enable", "sph_profile_reset", "sph_profile_read", "sph_launch_count",
-            "sph_grid_set_option", "sph_nnps_query_static"]
+            "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
+            "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static"]
 
 
 def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=None):
@@ -226,6 +227,13 @@ def sph_grid_csr(grid):
 
 def sph_profile_enable(on=True):
     _check(load().sph_profile_enable(1 if on else 0))
+
+
+def sph_profile_select(kernels=None):
+    """Time only the listed kernel tags (comma-separated string or list; None: all)."""
+    if kernels is not None and not isinstance(kernels, str):
+        kernels = ",".join(kernels)
+    _check(load().sph_profile_select(None if kernels is None else kernels.encode()))
 
 
 def sph_profile_reset():

@@ -236,3 +236,31 @@ def test_deterministic(sph):
     assert np.array_equal(a["rp"], b["rp"]) and np.array_equal(a["col"], b["col"])
     assert np.array_equal(a["rho"], b["rho"])
     assert np.array_equal(a["orig"], b["orig"])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_unaligned_coordinates(sph, dim):
+    """Coordinates at an address that is 8- but not 16-byte aligned (the
+    bounds pass then reads value by value) give the same CSR."""
+    ps = W.c1_2d_10k(side=37) if dim == 2 else W.c2_3d_1m(side=17)
+    flat = torch.zeros(ps.n * dim + 1, dtype=torch.float64, device="cuda")
+    flat[1:] = torch.from_numpy(ps.xyz.reshape(-1))
+    x = flat[1:].view(ps.n, dim)
+    assert x.data_ptr() % 16 == 8
+    g = sph.Grid(x, ps.h, ps.kh, order=1)
+    rp, col, rho = g.query()
+    rp_ref, col_ref = oracle.cll(ps.xyz, ps.kh)
+    assert np.array_equal(rp.cpu().numpy(), rp_ref) and np.array_equal(col.cpu().numpy(), col_ref)
+
+
+@pytest.mark.parametrize("where", ["first", "last"])
+def test_nonfinite_in_tail_rejected(sph, where):
+    """A non-finite value in the last (scalar tail) or first coordinate."""
+    xyz = W.random_uniform(101, 3, 2)  # 303 values: 50 six-value steps + a tail of 3
+    if where == "last":
+        xyz[100, 2] = np.inf
+    else:
+        xyz[0, 0] = -np.inf
+    with pytest.raises(sph.SphError) as ei:
+        sph.Grid(torch.from_numpy(xyz).cuda(), 0.05)
+    assert ei.value.code == sph.SPH_ERR_INVALID
