@@ -265,6 +265,13 @@ int sph_profile_select(const char *kernels);
 int sph_profile_reset(void);
 int sph_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
+/* Measured FP64 fused multiply-add throughput of the current CUDA device in
+ * FLOP/s (two per FMA): a short kernel of independent FMA chains timed with
+ * CUDA events on the legacy default stream (synchronises the device).  A
+ * diagnostic beside the FP64 cell link-list baseline; the paper's case for
+ * FP16 rests on the FP64 rate.  *flops: host pointer. */
+int sph_device_fp64_rate(double *flops);
+
 /* Number of kernels the library has launched since it was loaded. */
 int64_t sph_launch_count(void);
 

@@ -11,6 +11,7 @@ Functions and the passage each follows (arXiv 2401.08586):
   allpairs                -- all-list search (Section "SPH method", Fig. 3a).
   cll                     -- cell link-list search (same section, Fig. 3b).
   density                 -- summation density with W from Eq. 3 (self term included).
+  cll_rows / density_rows -- the same for a listed subset of rows (sampled checks).
   gradient_a5             -- normalised first-order gradient, Appendix Eq. A5.
 """
 import ctypes
@@ -42,6 +43,12 @@ def _load():
     lib.oracle_cll.restype = ctypes.c_int64
     lib.oracle_cll.argtypes = [ctypes.c_int, ctypes.c_int64, _f64p, ctypes.c_double, ctypes.c_int,
                                _i64p, _i32p, ctypes.c_int64]
+    lib.oracle_cll_rows.restype = ctypes.c_int64
+    lib.oracle_cll_rows.argtypes = [ctypes.c_int, ctypes.c_int64, _f64p, ctypes.c_double, ctypes.c_int,
+                                    _i64p, ctypes.c_int64, _i64p, _i32p, ctypes.c_int64]
+    lib.oracle_density_rows.restype = None
+    lib.oracle_density_rows.argtypes = [ctypes.c_int, _f64p, ctypes.c_double, ctypes.c_double, _i64p,
+                                        ctypes.c_int64, _i64p, _i32p, _f64p]
     lib.oracle_density.restype = None
     lib.oracle_density.argtypes = [ctypes.c_int, ctypes.c_int64, _f64p, ctypes.c_double,
                                    ctypes.c_double, _i64p, _i32p, ctypes.c_int, _f64p]
@@ -101,6 +108,52 @@ def allpairs(xyz, kh):
 def cll(xyz, kh, threads=1):
     """Cell link-list neighbour CSR, same contract as :func:`allpairs`."""
     return _csr(_load().oracle_cll, xyz, kh, int(threads))
+
+
+def cll_counts(xyz, kh, threads=1):
+    """Row pointer of the cell link-list CSR only (no column array)."""
+    xyz = _coords(xyz)
+    n, dim = xyz.shape
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    nnz = _load().oracle_cll(dim, n, _ptr(xyz, _f64p), float(kh), int(threads), _ptr(row_ptr, _i64p), None, 0)
+    if nnz < 0:
+        raise ValueError("domain too large for the oracle's cell grid")
+    return row_ptr
+
+
+def cll_rows(xyz, kh, rows, threads=1):
+    """Neighbour lists (ascending input indices) of the listed particles only:
+    CSR with one row per entry of ``rows``."""
+    xyz = _coords(xyz)
+    n, dim = xyz.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= n):
+        raise ValueError("row index out of range")
+    rp = np.zeros(rows.size + 1, dtype=np.int64)
+    lib = _load()
+    nnz = lib.oracle_cll_rows(dim, n, _ptr(xyz, _f64p), float(kh), int(threads), _ptr(rows, _i64p), rows.size,
+                              _ptr(rp, _i64p), None, 0)
+    if nnz < 0:
+        raise ValueError("grid too large")
+    col = np.empty(max(nnz, 1), dtype=np.int32)
+    lib.oracle_cll_rows(dim, n, _ptr(xyz, _f64p), float(kh), int(threads), _ptr(rows, _i64p), rows.size,
+                        _ptr(rp, _i64p), _ptr(col, _i32p), col.size)
+    return rp, col[:nnz]
+
+
+def density_rows(xyz, h, rows, row_ptr, col, mass=1.0):
+    """FP64 summation density of the listed particles, given their rows."""
+    xyz = _coords(xyz)
+    dim = xyz.shape[1]
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    rho = np.empty(rows.size, dtype=np.float64)
+    _load().oracle_density_rows(dim, _ptr(xyz, _f64p), float(h), float(mass), _ptr(rows, _i64p), rows.size,
+                                _ptr(row_ptr, _i64p), _ptr(col, _i32p), _ptr(rho, _f64p))
+    return rho
 
 
 def density(xyz, h, row_ptr, col, mass=1.0, threads=1):

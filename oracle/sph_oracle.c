@@ -24,6 +24,9 @@
  *       to cells, and only the same and adjacent cells searched.  It finds the
  *       same set as oracle_allpairs (the paper notes the two give identical
  *       neighbour decisions, Table 2).
+ *   oracle_cll_rows / oracle_density_rows
+ *       the same two computations for a listed subset of rows (sampled
+ *       checks of workloads too large for a full oracle pass).
  *   oracle_density
  *       summation density rho_i = sum_j m_j W(r_ij / h, h) over the neighbour
  *       list plus the self term j = i (the textbook SPH density; W from Eq. 3).
@@ -309,6 +312,77 @@ int64_t oracle_cll(int dim, int64_t n, const double *xyz, double kh, int nthread
     free(cnt);
     grid_free(&g);
     return nnz;
+}
+
+/*
+ * The cell link-list search restricted to the listed rows (input indices
+ * rows[0..nrows)): row r of the output is particle rows[r]'s neighbour list,
+ * ascending.  Same grid and decisions as oracle_cll, for checking sampled rows
+ * of a workload too large to search in full.  Returns the total count, or -1
+ * as oracle_cll; col is written only when cap is large enough.
+ */
+int64_t oracle_cll_rows(int dim, int64_t n, const double *xyz, double kh, int nthreads,
+                        const int64_t *rows, int64_t nrows, int64_t *row_ptr, int32_t *col, int64_t cap)
+{
+    oracle_grid g;
+    if (grid_build(dim, n, xyz, kh, &g) != 0) return -1;
+    double kh2 = kh * kh;
+    int64_t maxc = max_candidates(&g) + 1;
+    if (nthreads < 1) nthreads = 1;
+    int64_t *cnt = (int64_t *)malloc((size_t)(nrows > 0 ? nrows : 1) * sizeof(int64_t));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        int32_t *buf = (int32_t *)malloc((size_t)maxc * sizeof(int32_t));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t r = 0; r < nrows; ++r) cnt[r] = cll_row(&g, n, xyz, kh2, rows[r], buf);
+        free(buf);
+    }
+    row_ptr[0] = 0;
+    for (int64_t r = 0; r < nrows; ++r) row_ptr[r + 1] = row_ptr[r] + cnt[r];
+    int64_t nnz = row_ptr[nrows];
+    if (col != NULL && cap >= nnz) {
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+        {
+            int32_t *buf = (int32_t *)malloc((size_t)maxc * sizeof(int32_t));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+            for (int64_t r = 0; r < nrows; ++r) {
+                int64_t f = cll_row(&g, n, xyz, kh2, rows[r], buf);
+                memcpy(col + row_ptr[r], buf, (size_t)f * sizeof(int32_t));
+            }
+            free(buf);
+        }
+    }
+    free(cnt);
+    grid_free(&g);
+    return nnz;
+}
+
+/*
+ * Summation density of the listed rows only: rho[r] for particle rows[r],
+ * whose neighbours are col[row_ptr[r] .. row_ptr[r + 1]) (input indices).
+ * Same sum, order and arithmetic as oracle_density.
+ */
+void oracle_density_rows(int dim, const double *xyz, double h, double mass, const int64_t *rows, int64_t nrows,
+                         const int64_t *row_ptr, const int32_t *col, double *rho)
+{
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        double s = mass * oracle_kernel_w(dim, 0.0, h);
+        for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            int64_t j = col[k];
+            double d = sqrt(pair_r2(dim, xyz + i * dim, xyz + j * dim));
+            s += mass * oracle_kernel_w(dim, d / h, h);
+        }
+        rho[r] = s;
+    }
 }
 
 /*

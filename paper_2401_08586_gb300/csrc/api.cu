@@ -617,6 +617,15 @@ extern "C" int sph_profile_select(const char *kernels) {
     return SPH_OK;
 }
 
+extern "C" int sph_device_fp64_rate(double *flops) {
+    if (!flops) return fail(SPH_ERR_INVALID, "NULL argument");
+    if (fp64_fma_rate(flops) != 0) {
+        cudaGetLastError();
+        return fail(SPH_ERR_CUDA, "FP64 rate measurement failed");
+    }
+    return SPH_OK;
+}
+
 extern "C" int sph_profile_reset(void) {
     prof_reset();
     return SPH_OK;

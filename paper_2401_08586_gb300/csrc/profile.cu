@@ -124,3 +124,55 @@ int prof_read(const char *name, double *ms, long long *calls) {
 }
 
 }  // namespace sph
+
+// ---- FP64 FMA throughput of the device ---------------------------------------
+// Eight independent FMA chains per thread keep the FP64 pipe busy; the result
+// is stored so that nothing is optimised away.
+namespace sph {
+namespace {
+constexpr int FP64_CHAINS = 8;
+constexpr int FP64_ITERS = 2048;
+
+__global__ void k_fp64_fma(double *out, double a, double b) {
+    double v[FP64_CHAINS];
+#pragma unroll
+    for (int c = 0; c < FP64_CHAINS; ++c) v[c] = (double)(threadIdx.x + c);
+    for (int it = 0; it < FP64_ITERS; ++it) {
+#pragma unroll
+        for (int c = 0; c < FP64_CHAINS; ++c) v[c] = __fma_rn(v[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < FP64_CHAINS; ++c) s += v[c];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+int fp64_fma_rate(double *flops) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    const int nt = 256, blocks = sms * 8;
+    double *out = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * nt * sizeof(double)) != cudaSuccess) return -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    note_launch(1);
+    k_fp64_fma<<<blocks, nt>>>(out, 0.999999, 1e-7);  // warm-up
+    cudaEventRecord(a);
+    const int reps = 5;
+    note_launch(reps);
+    for (int r = 0; r < reps; ++r) k_fp64_fma<<<blocks, nt>>>(out, 0.999999, 1e-7);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (e != cudaSuccess || ms <= 0.f) return -1;
+    *flops = 2.0 * (double)reps * blocks * nt * FP64_CHAINS * FP64_ITERS / (ms * 1e-3);
+    return 0;
+}
+}  // namespace sph

@@ -45,6 +45,8 @@ void prof_enable(int on);
 // Enable timing for a comma-separated list of tag names only (NULL: all);
 // -1 if a name is unknown (nothing changed).
 int prof_select(const char *names);
+// Measured FP64 FMA throughput of the current device, in FLOP/s (2 per FMA).
+int fp64_fma_rate(double *flops);
 void prof_reset();
 int prof_read(const char *name, double *ms, long long *calls);
 

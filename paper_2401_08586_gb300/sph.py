@@ -92,6 +92,7 @@ def load(build_if_missing=False):
         "sph_profile_enable": [ctypes.c_int],
         "sph_profile_reset": [],
         "sph_profile_select": [ctypes.c_char_p],
+        "sph_device_fp64_rate": [ctypes.POINTER(ctypes.c_double)],
         "sph_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "sph_launch_count": [],
         "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
@@ -112,7 +113,7 @@ def exported_symbols():
             "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
-            "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static"]
+            "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate"]
 
 
 def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=None):
@@ -234,6 +235,13 @@ def sph_profile_select(kernels=None):
     if kernels is not None and not isinstance(kernels, str):
         kernels = ",".join(kernels)
     _check(load().sph_profile_select(None if kernels is None else kernels.encode()))
+
+
+def sph_device_fp64_rate():
+    """Measured FP64 FMA throughput of the current device, FLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load().sph_device_fp64_rate(ctypes.byref(v)))
+    return v.value
 
 
 def sph_profile_reset():

@@ -128,6 +128,21 @@ def test_cll_equals_allpairs(name, xyz, kh):
     assert np.array_equal(col_a, col_c)
 
 
+@pytest.mark.parametrize("name,xyz,kh", [c for c in _cases() if c[1].shape[0] >= 2],
+                         ids=[c[0] for c in _cases() if c[1].shape[0] >= 2])
+def test_cll_rows_equal_allpairs_rows(name, xyz, kh):
+    """Sampled rows (shuffled, repeated) are the brute-force rows."""
+    rp_a, col_a = oracle.allpairs(xyz, kh)
+    rng = np.random.default_rng(3)
+    rows = rng.integers(0, xyz.shape[0], size=min(300, 3 * xyz.shape[0]))
+    rp, col = oracle.cll_rows(xyz, kh, rows, threads=2)
+    for r, i in enumerate(rows):
+        assert np.array_equal(col[rp[r]:rp[r + 1]], col_a[rp_a[i]:rp_a[i + 1]])
+    rho = oracle.density_rows(xyz, 0.5 * kh, rows, rp, col)
+    rho_all = oracle.density(xyz, 0.5 * kh, rp_a, col_a)
+    assert np.array_equal(rho, rho_all[rows])
+
+
 def test_cll_threads_identical():
     ps = W.c2_3d_1m(side=20)
     a = oracle.cll(ps.xyz, ps.kh, threads=1)
