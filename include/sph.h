@@ -208,6 +208,13 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *       2 single pass, one thread block per cell, look-back across cells;
  *       0 two passes (count pass, row scan, fill pass). */
 #define SPH_OPT_FUSED 1
+/*   SPH_OPT_STAGING: bytes of shared memory the tile search (SPH_OPT_FUSED 1)
+ *     adds to its output staging area: -1 (default) sizes it from the
+ *     neighbours per particle of the grid's last query that reported nnz
+ *     (else from the particle density), 0 .. 65536 in multiples of 16 fix it.
+ *     A tile whose output does not fit writes its rows directly (same
+ *     result); more staging lowers the number of resident warps. */
+#define SPH_OPT_STAGING 2
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 
 /* Fill *info (host) with the grid's sizes and device pointers.  The pointers
@@ -249,6 +256,76 @@ int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, floa
  * sph_search_host on this grid (host out-pointers; any may be NULL). */
 int sph_grid_csr(sph_grid_t grid, const int64_t **row_ptr, const int32_t **col, const float **rho,
                  int64_t *nnz);
+
+/* ---- Batched runs: many independent systems in one pass ----------------------
+ *
+ * sph_batch_run bins, searches and sums the density of nsys independent
+ * particle systems (all of one dimension, FP16-RCLL, cell order) as one
+ * concatenated problem: one launch per binning step and one persistent
+ * launch of the tile search for all systems.  The paper searches one system
+ * at a time; batching is this library's way of filling the GPU with many
+ * small ones.
+ *
+ * The output is one block-diagonal CSR over the concatenation in cell order:
+ * system s owns sorted positions (= rows) [sys_first[s], sys_first[s+1]),
+ * its columns are sorted positions of the same range, ascending within each
+ * row, and orig_id maps a sorted position to the system's own input index.
+ *
+ * per_system, xyz (host array of nsys device pointers, each n[s] x dim FP64),
+ * n (host) describe the systems; params as for sph_bin_cells (have_box per
+ * system; order must be SPH_ORDER_CELL, precision SPH_PREC_FP16_RCLL).
+ * *batch: workspace, created on first use (pass a pointer to NULL) and reused;
+ * it owns the device buffers, the recorded CUDA graph and the tuning cache.
+ * The call synchronises `stream` (it reads the systems' bounds and nnz).
+ *
+ * Errors: SPH_ERR_INVALID (parameters, mixed dims, more than 2^31 - 1
+ * particles or cells in total), SPH_ERR_CAPACITY (nnz > col_capacity: out->nnz
+ * is set, no entry at or past col_capacity is written), others as
+ * sph_bin_cells.
+ */
+typedef struct sph_batch_s *sph_batch_t;
+
+typedef struct {
+    int64_t *row_ptr;     /* device int64[n_total + 1], written (global offsets into col) */
+    int32_t *col;         /* device int32[col_capacity], or NULL: row_ptr, rho and nnz only */
+    int64_t col_capacity;
+    float *rho;           /* device float[n_total] (sorted positions), or NULL; needs col */
+    int32_t *orig_id;     /* device int32[n_total] or NULL: sorted position -> the system's input index */
+    int64_t *sys_first;   /* host int64[nsys + 1] or NULL: first sorted position of each system */
+    int64_t nnz;          /* written: total neighbour count */
+} sph_batch_out;
+
+/* Create an empty workspace (host call; binds to the current CUDA device). */
+int sph_batch_create(sph_batch_t *batch);
+
+int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, const double *const *xyz, const int64_t *n,
+                  int nsys, sph_batch_out *out, void *stream);
+
+/* Counters of a workspace (host struct). */
+typedef struct {
+    int64_t runs;             /* sph_batch_run calls */
+    int64_t graph_captures;   /* launch sequences recorded as CUDA graphs */
+    int64_t graph_replays;    /* runs that replayed the recorded graph */
+    int32_t tuned_staging;    /* staging bytes chosen by the last tuning, -1: none yet */
+    int32_t tuned_candidates; /* candidates timed by the last tuning */
+    int64_t fp32_pairs;       /* last run: pairs re-decided in FP32 */
+    int64_t fp64_pairs;       /* last run: pairs decided in FP64 */
+} sph_batch_stats;
+int sph_batch_get_stats(sph_batch_t batch, sph_batch_stats *stats);
+
+/* SPH_BATCH_OPT_GRAPH: 1 (default) record the launch sequence after the
+ *   bounds as a CUDA graph and replay it while the batch's sizes and buffers
+ *   are unchanged; 0 launch directly every time.
+ * SPH_BATCH_OPT_STAGING: -1 (default) tune the tile search's staging bytes by
+ *   timing 0, 2048, 4096 and 8192 on the first run of each density class
+ *   (dimension and neighbours per particle to a quarter octave) and reuse the
+ *   winner; 0 .. 65536 in multiples of 16 fix it. */
+#define SPH_BATCH_OPT_GRAPH 1
+#define SPH_BATCH_OPT_STAGING 2
+int sph_batch_set_option(sph_batch_t batch, int option, int64_t value);
+
+/* Free a workspace (synchronises the device).  NULL is a no-op. */
+int sph_batch_free(sph_batch_t batch);
 
 /* Per-kernel device timing of the library's own launches.  While enabled,
  * every launch is bracketed by CUDA events recorded on its stream.

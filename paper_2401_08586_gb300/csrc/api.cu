@@ -9,72 +9,13 @@
 #include <new>
 #include <string>
 
+#include "host.cuh"
+#include "launch.cuh"
 #include "profile.cuh"
 #include "sph_internal.cuh"
 
-namespace sph {
-cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count,
-                          cudaStream_t s);
-cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec,
-                                        int *cnt, int *cid, int *slot, int *cell_start, int *orig_id,
-                                        int *rank, int *scell, uint2 *rel16, float4 *rel32, uint2 *rel16u,
-                                        float4 *rel32u, double4 *x64,
-                                        void *scan_tmp, int *big_list, unsigned int *big_count,
-                                        int check_box, int sm_count, cudaStream_t s);
-cudaError_t launch_nnps(const GridDev &g, int prec, int mode_fill, int *cnt, const long long *row_ptr,
-                        int *col, long long cap, float *rho, int sm_count, cudaStream_t s);
-cudaError_t launch_density(const GridDev &g, int prec, const int *rank, const int *scell,
-                           const long long *row_ptr, const int *col, int canonical, float *rho,
-                           int sm_count, cudaStream_t s);
-cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, long long cap, float *rho,
-                              unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);
-cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
-                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
-cudaError_t launch_nnps_tile(const GridDev &g, const int4 *tiles, const long long *ntiles_dev, long long ntiles_max,
-                             long long *row_ptr, int *col, long long cap, float *rho, unsigned long long *tstate,
-                             int sm_count, cudaStream_t s);
-cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long long *rp_cell,
-                         const int *col_cell, const float *rho_cell, int *cnt_tmp, void *scan_tmp,
-                         long long *rp, int *col, float *rho, int *big_list, unsigned int *big_count,
-                         int sm_count, cudaStream_t s);
-
-__global__ void k_status_init(DevStatus *st) {
-    st->flags = 0;
-    st->big_cells = 0;
-    for (int a = 0; a < 3; ++a) {
-        st->min_key[a] = ~0ull;
-        st->max_key[a] = 0ull;
-    }
-    st->fp32_pairs = 0;
-    st->fp64_pairs = 0;
-    st->nnz = 0;
-    st->ticket = 0;
-}
-
-__global__ void k_status_reset_counters(DevStatus *st) {
-    st->fp32_pairs = 0;
-    st->fp64_pairs = 0;
-    st->ticket = 0;
-}
-}  // namespace sph
 
 using namespace sph;
-
-// Error band of the FP16 "maybe" test and of the FP32 re-decision, in units
-// of u^2 (u = h_c / 2).  Derivation (worst case over all pairs with r < kh,
-// |x_rel| <= 1): FP16 rounding of x_rel <= 2^-12, of the pre-shifted
-// candidate <= 2^-10, of the difference <= 2^-10, so |d - D| <= 2.5 * 2^-10
-// per axis; squaring over three axes with |D| <= 2 adds <= 0.0169 and the
-// three rounded FMAs of e = d^2 - T add <= 3 * 2^-10: 0.0199 < 0.03.  FP32:
-// |d - D| <= 2 * 2^-25 + 2 * 2^-23 per axis -> <= 3.8e-6, plus three FMA
-// roundings <= 7.2e-7 and the FP32 rounding of T: 4.7e-6 < 8e-6.
-static const double TAU16 = 0.03;
-static const double TAU32 = 8e-6;
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-};
 
 struct sph_grid_s {
     sph_params p;
@@ -91,87 +32,11 @@ struct sph_grid_s {
         rowcnt, tmp_rp, tmp_col, tmp_rho, status, own_xyz, own_rp, own_col, own_rho, tstate, scell_x, tcount,
         toff, tiles;
     int fused_enabled = 1;  // search variant for cell-order FP16 queries (SPH_OPT_FUSED)
+    int staging = -1;       // extra staging bytes of the tile search (SPH_OPT_STAGING; -1: automatic)
+    double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
     long long own_nnz = 0;
     DevStatus *h_status = nullptr;  // pinned host mirror
 };
-
-static thread_local std::string g_err;
-
-static int fail(int code, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
-    va_end(ap);
-    g_err = buf;
-    return code;
-}
-
-#define SPH_CUDA(x)                                                                        \
-    do {                                                                                   \
-        cudaError_t e_ = (x);                                                              \
-        if (e_ != cudaSuccess) {                                                           \
-            cudaGetLastError();                                                            \
-            return fail(SPH_ERR_CUDA, "%s failed: %s", #x, cudaGetErrorString(e_));        \
-        }                                                                                  \
-    } while (0)
-
-#define SPH_TRY(x)                   \
-    do {                             \
-        int r_ = (x);                \
-        if (r_ != SPH_OK) return r_; \
-    } while (0)
-
-static int ensure(DevBuf &b, size_t bytes, cudaStream_t s) {
-    if (bytes == 0) bytes = 16;
-    if (bytes <= b.cap) return SPH_OK;
-    if (b.p) cudaFreeAsync(b.p, s);
-    b.p = nullptr;
-    b.cap = 0;
-    size_t want = bytes + bytes / 8 + 256;
-    cudaError_t e = cudaMallocAsync(&b.p, want, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(SPH_ERR_NOMEM, "device allocation of %zu bytes failed: %s", want,
-                    cudaGetErrorString(e));
-    }
-    b.cap = want;
-    return SPH_OK;
-}
-
-static void release(DevBuf &b, cudaStream_t s) {
-    if (b.p) cudaFreeAsync(b.p, s);
-    b.p = nullptr;
-    b.cap = 0;
-}
-
-template <typename T>
-static T *P(DevBuf &b) {
-    return reinterpret_cast<T *>(b.p);
-}
-
-static double kernel_alpha(int dim, double h) {
-    const double pi = 3.14159265358979323846;
-    return dim == 2 ? 15.0 / (7.0 * pi * h * h) : 3.0 / (2.0 * pi * h * h * h);
-}
-
-static float f32_down(double x) {
-    float f = (float)x;
-    if ((double)f > x) f = nextafterf(f, -INFINITY);
-    return f;
-}
-static float f32_up(double x) {
-    float f = (float)x;
-    if ((double)f < x) f = nextafterf(f, INFINITY);
-    return f;
-}
-
-static unsigned int half2_splat_bits(__half h) {
-    __half2 v = __halves2half2(h, h);
-    unsigned int u;
-    memcpy(&u, &v, 4);
-    return u;
-}
 
 static GridDev make_dev(sph_grid_s *g) {
     GridDev d;
@@ -192,41 +57,9 @@ static GridDev make_dev(sph_grid_s *g) {
     d.orig_id = P<int>(g->orig_id);
     d.scell_x = P<int>(g->scell_x);
     d.xyz = g->xyz;
-    const double kh = g->p.kh, h = g->p.h;
-    d.kh2 = kh * kh;
-    const double u = g->hc * 0.5;
-    const double T = d.kh2 / (u * u);
-    d.t32_in = f32_down(T - TAU32);
-    d.t32_out = f32_up(T + TAU32);
-    // FP16 threshold rounded upward so that e = r2 - T16 never exceeds r2 - T.
-    __half t16 = __double2half(T);
-    if ((double)__half2float(t16) < T) t16 = __float2half_rn(nextafterf(__half2float(t16), INFINITY));
-    while ((double)__half2float(t16) < T) {
-        unsigned short b;
-        memcpy(&b, &t16, 2);
-        ++b;
-        memcpy(&t16, &b, 2);
-    }
-    d.neg_t16 = half2_splat_bits(__hneg(t16));
-    d.tau16 = half2_splat_bits(__double2half(TAU16));
-    const double alpha = kernel_alpha(g->p.dim, h);
-    d.r_scale = (float)(u / h);
-    d.w_norm = (float)(g->p.mass * alpha);
-    d.w_self = (float)(g->p.mass * alpha * (2.0 / 3.0));
-    d.r_scale64 = 1.0 / h;
-    d.w_norm64 = g->p.mass * alpha;
-    d.w_self64 = g->p.mass * alpha * (2.0 / 3.0);
+    set_constants(d, g->p, g->hc);
     d.status = P<DevStatus>(g->status);
     return d;
-}
-
-static int status_to_code(unsigned int flags) {
-    if (flags & ST_NONFINITE) return fail(SPH_ERR_INVALID, "non-finite particle coordinate");
-    if (flags & ST_OUT_OF_BOX) return fail(SPH_ERR_INVALID, "particle outside the given box");
-    if (flags & ST_TIMEOUT) return fail(SPH_ERR_TIMEOUT, "a bounded device wait ran out");
-    if (flags & ST_CAPACITY) return fail(SPH_ERR_CAPACITY, "nnz exceeds col_capacity");
-    if (flags & ST_DEVICE_CHECK) return fail(SPH_ERR_DEVICE_CHECK, "device consistency check failed");
-    return SPH_OK;
 }
 
 // Copy the status record to the host mirror and wait.
@@ -234,29 +67,6 @@ static int read_status(sph_grid_s *g) {
     SPH_CUDA(cudaMemcpyAsync(g->h_status, g->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                              g->stream));
     SPH_CUDA(cudaStreamSynchronize(g->stream));
-    return SPH_OK;
-}
-
-static int validate(const sph_params *p, int64_t n, const double *xyz) {
-    if (!p) return fail(SPH_ERR_INVALID, "params is NULL");
-    if (p->dim != 2 && p->dim != 3) return fail(SPH_ERR_INVALID, "dim must be 2 or 3 (got %d)", p->dim);
-    if (p->order != SPH_ORDER_CELL && p->order != SPH_ORDER_CANONICAL)
-        return fail(SPH_ERR_INVALID, "unknown order %d", p->order);
-    if (p->precision != SPH_PREC_FP16_RCLL && p->precision != SPH_PREC_FP64_CLL)
-        return fail(SPH_ERR_INVALID, "unknown precision %d", p->precision);
-    if (!(p->kh > 0) || !isfinite(p->kh)) return fail(SPH_ERR_INVALID, "kh must be finite and > 0");
-    if (!(p->h > 0) || !isfinite(p->h)) return fail(SPH_ERR_INVALID, "h must be finite and > 0");
-    if (!isfinite(p->mass)) return fail(SPH_ERR_INVALID, "mass must be finite");
-    const double hc_min = p->kh * (1.0 + 0x1p-30);
-    if (p->cell_size != 0 && !(p->cell_size >= hc_min && isfinite(p->cell_size)))
-        return fail(SPH_ERR_INVALID, "cell_size must be 0 or >= kh * (1 + 2^-30)");
-    if (n < 0 || n >= 0x7fffffffLL) return fail(SPH_ERR_INVALID, "n out of range: %lld", (long long)n);
-    if (n > 0 && xyz == nullptr) return fail(SPH_ERR_INVALID, "xyz is NULL");
-    if (p->have_box) {
-        for (int k = 0; k < p->dim; ++k)
-            if (!isfinite(p->box_lo[k]) || !isfinite(p->box_hi[k]) || !(p->box_hi[k] >= p->box_lo[k]))
-                return fail(SPH_ERR_INVALID, "invalid box on axis %d", k);
-    }
     return SPH_OK;
 }
 
@@ -268,7 +78,7 @@ extern "C" int sph_precision_bands(double *tau16, double *tau32) {
     return SPH_OK;
 }
 
-extern "C" const char *sph_last_error(void) { return g_err.c_str(); }
+extern "C" const char *sph_last_error(void) { return last_error(); }
 
 static int grid_create(sph_grid_s **out) {
     sph_grid_s *g = new (std::nothrow) sph_grid_s();
@@ -288,7 +98,7 @@ static int grid_create(sph_grid_s **out) {
 extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, void *stream,
                              sph_grid_t *grid) {
     if (!grid) return fail(SPH_ERR_INVALID, "grid is NULL");
-    SPH_TRY(validate(p, n, xyz));
+    SPH_TRY(validate_params(p, n, xyz));
     bool created = false;
     if (*grid == nullptr) {
         SPH_TRY(grid_create(grid));
@@ -305,8 +115,11 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
     int rc = SPH_OK;
     do {
         if ((rc = ensure(g->status, sizeof(DevStatus), s)) != SPH_OK) break;
-        note_launch(1);
-        k_status_init<<<1, 1, 0, s>>>(P<DevStatus>(g->status));
+        if (launch_status_init(P<DevStatus>(g->status), s) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(SPH_ERR_CUDA, "status launch failed");
+            break;
+        }
         double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
         if (p->have_box) {
             for (int k = 0; k < dim; ++k) {
@@ -408,8 +221,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         return SPH_OK;
     }
     GridDev d = make_dev(g);
-    note_launch(1);
-    k_status_reset_counters<<<1, 1, 0, s>>>(P<DevStatus>(g->status));
+    SPH_CUDA(launch_status_reset_counters(P<DevStatus>(g->status), s));
     SPH_TRY(ensure(g->rowcnt, n * sizeof(int), s));
     const bool canonical = g->p.order == SPH_ORDER_CANONICAL;
     const int prec = g->p.precision;
@@ -436,8 +248,20 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         d = make_dev(g);
         SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), P<int>(g->tcount), P<long long>(g->toff),
                               g->scan_tmp.p, P<int4>(g->tiles), g->sm_count, s));
-        SPH_CUDA(launch_nnps_tile(d, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell, col,
-                                  col_capacity, rho, P<unsigned long long>(g->tstate), g->sm_count, s));
+        int extra = g->staging;
+        if (extra < 0) {
+            // neighbours per particle: the last measured value, else the
+            // uniform-density estimate (particles per cell x the search
+            // sphere's volume in cells)
+            double nbr = g->last_nbr;
+            if (nbr <= 0) {
+                const double ppc = (double)n / (double)g->ncell, r = g->p.kh / g->hc;
+                nbr = g->p.dim == 3 ? ppc * 4.18879 * r * r * r : ppc * 3.14159 * r * r;
+            }
+            extra = tile_extra_smem(nbr);
+        }
+        SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell,
+                                  col, col_capacity, rho, P<unsigned long long>(g->tstate), extra, g->sm_count, s));
     } else {
         SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
         SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
@@ -450,6 +274,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
             long long nnz_host = 0;
             SPH_CUDA(cudaStreamSynchronize(s));
             nnz_host = g->h_status->nnz;
+            if (n > 0) g->last_nbr = (double)nnz_host / (double)n;
             SPH_TRY(read_status(g));
             *nnz_out = nnz_host;
             int rc = status_to_code(g->h_status->flags);
@@ -465,6 +290,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
     SPH_CUDA(cudaMemcpyAsync(&g->h_status->nnz, rp_cell + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
     SPH_CUDA(cudaStreamSynchronize(s));
     nnz = g->h_status->nnz;
+    g->last_nbr = (double)nnz / (double)n;
     if (nnz_out) *nnz_out = nnz;
     if (col && nnz > col_capacity) {
         SPH_TRY(launch_canon((int)n, P<int>(g->rank), P<int>(g->orig_id), rp_cell, nullptr, nullptr,
@@ -551,6 +377,12 @@ extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
         g->fused_enabled = (int)value;
         return SPH_OK;
     }
+    if (option == SPH_OPT_STAGING) {
+        if (value < -1 || value > 65536 || (value > 0 && value % 16 != 0))
+            return fail(SPH_ERR_INVALID, "SPH_OPT_STAGING takes -1 or a multiple of 16 in [0, 65536]");
+        g->staging = (int)value;
+        return SPH_OK;
+    }
     return fail(SPH_ERR_INVALID, "unknown option %d", option);
 }
 
@@ -566,7 +398,7 @@ extern "C" int sph_grid_check(sph_grid_t grid, void *stream) {
 extern "C" int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, float *rho_host,
                                int64_t *nnz_host, sph_grid_t *grid, void *stream) {
     if (!grid) return fail(SPH_ERR_INVALID, "grid is NULL");
-    SPH_TRY(validate(p, n, xyz_host));
+    SPH_TRY(validate_params(p, n, xyz_host));
     cudaStream_t s = (cudaStream_t)stream;
     if (*grid == nullptr) SPH_TRY(grid_create(grid));
     sph_grid_s *g = *grid;
@@ -658,10 +490,7 @@ int grid_view(sph_grid_t grid, GridView *v) {
 
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
-void reset_counters_async(DevStatus *st, cudaStream_t s) {
-    note_launch(1);
-    k_status_reset_counters<<<1, 1, 0, s>>>(st);
-}
+void reset_counters_async(DevStatus *st, cudaStream_t s) { launch_status_reset_counters(st, s); }
 
 }  // namespace sph
 

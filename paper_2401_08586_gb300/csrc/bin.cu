@@ -20,6 +20,7 @@
 //              the FP64 cell link-list, the FP64 coordinate.
 // The FP64 work is one pass of five operations per axis: this part's FP64
 // rate is a small fraction of its FP32 and integer rates.
+#include "launch.cuh"
 #include "profile.cuh"
 #include "sph_internal.cuh"
 
@@ -97,23 +98,6 @@ __global__ void k_bounds(const double *__restrict__ xyz, long long total, int di
             atomicMax(&st->max_key[a], vmx);
         }
     }
-}
-
-// Cell index and cell-relative coordinate of one axis, in units of
-// u = h_c / 2 (Eq. 6 with the cell centre as reference):
-//   s = 2 (x - lo) / h_c,  c = clamp(floor(s / 2), 0, nk - 1),
-//   a = s - (2c + 1)  (exact: s and 2c + 1 are within one of each other).
-// Five FP64 operations and no division.  s carries a relative error of at
-// most 2^-52 (x - lo is exact whenever x and lo are within a factor of two),
-// i.e. at most 2^-31 u at the 2^20-cell limit, below the 2^-29 u margin that
-// the cell size kh (1 + 2^-30) leaves, so every pair closer than kh sits in
-// the same or adjacent cells.
-__device__ __forceinline__ int rel_axis(double x, double lo, double two_over_hc, int nk, double &a) {
-    const double s = __dmul_rn(__dsub_rn(x, lo), two_over_hc);
-    int c = __double2int_rd(s) >> 1;  // floor(floor(s) / 2) = floor(s / 2); saturating conversion
-    c = min(max(c, 0), nk - 1);
-    a = __dsub_rn(s, (double)(2 * c + 1));
-    return c;
 }
 
 template <int PREC>
@@ -198,6 +182,14 @@ static unsigned grid_for(long long n, int nt, int sm_count, int per_sm) {
     long long b = (n + nt - 1) / nt;
     if (b > (long long)sm_count * per_sm) b = (long long)sm_count * per_sm;
     return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_scatter(int n, const int *cell_start, const int *cid, const int *slot, int *orig_id,
+                           int sm_count, cudaStream_t s) {
+    ProfScope ps(TAG_SCATTER, s);
+    note_launch(1);
+    k_scatter<<<grid_for(n, 256, sm_count, 16), 256, 0, s>>>(n, cell_start, cid, slot, orig_id);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count,

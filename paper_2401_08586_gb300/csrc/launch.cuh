@@ -1,0 +1,42 @@
+// launch.cuh -- host launchers of the library's kernels, one per step of the
+// path (defined next to their kernels: bin.cu, search.cu, nnps_fused.cu,
+// nnps_tile.cu, batch.cu).  All enqueue on stream s and return the launch
+// status; none synchronises.
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// Binning (bin.cu).
+cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count, cudaStream_t s);
+cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec, int *cnt,
+                                        int *cid, int *slot, int *cell_start, int *orig_id, int *rank, int *scell,
+                                        uint2 *rel16, float4 *rel32, uint2 *rel16u, float4 *rel32u, double4 *x64,
+                                        void *scan_tmp, int *big_list, unsigned int *big_count, int check_box,
+                                        int sm_count, cudaStream_t s);
+cudaError_t launch_scatter(int n, const int *cell_start, const int *cid, const int *slot, int *orig_id,
+                           int sm_count, cudaStream_t s);
+
+// Two-pass search, unfused density, canonical order (search.cu).
+cudaError_t launch_nnps(const GridDev &g, int prec, int mode_fill, int *cnt, const long long *row_ptr, int *col,
+                        long long cap, float *rho, int sm_count, cudaStream_t s);
+cudaError_t launch_density(const GridDev &g, int prec, const int *rank, const int *scell, const long long *row_ptr,
+                           const int *col, int canonical, float *rho, int sm_count, cudaStream_t s);
+cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long long *rp_cell, const int *col_cell,
+                         const float *rho_cell, int *cnt_tmp, void *scan_tmp, long long *rp, int *col, float *rho,
+                         int *big_list, unsigned int *big_count, int sm_count, cudaStream_t s);
+
+// Single-pass search, one CTA per cell (nnps_fused.cu).
+cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, long long cap, float *rho,
+                              unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);
+
+// Single-pass search, one warp per row tile (nnps_tile.cu).
+cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
+                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
+cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
+                             long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
+                             unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s);
+int tile_extra_smem(double neighbours_per_particle);
+
+}  // namespace sph

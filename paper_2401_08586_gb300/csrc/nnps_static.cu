@@ -10,15 +10,10 @@
 // for the array's device address and caches it.
 #include <mutex>
 
+#include "launch.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
-
-cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
-                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
-cudaError_t launch_nnps_tile(const GridDev &g, const int4 *tiles, const long long *ntiles_dev, long long ntiles_max,
-                             long long *row_ptr, int *col, long long cap, float *rho, unsigned long long *tstate,
-                             int sm_count, cudaStream_t s);
 
 namespace {
 
@@ -110,8 +105,8 @@ extern "C" int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t 
     reset_counters_async(d.status, s);
     cudaError_t e = launch_tiles(d, v.scell, scell_x, tcount, toff, scan_tmp, tiles, v.sm_count, s);
     if (e == cudaSuccess)
-        e = launch_nnps_tile(d, tiles, toff + v.nrow, ntiles_max, reinterpret_cast<long long *>(row_ptr), col,
-                             col_capacity, rho, tstate, v.sm_count, s);
+        e = launch_nnps_tile(d, nullptr, tiles, toff + v.nrow, ntiles_max, reinterpret_cast<long long *>(row_ptr), col,
+                             col_capacity, rho, tstate, 0, v.sm_count, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(SPH_ERR_CUDA, cudaGetErrorString(e));

@@ -43,7 +43,7 @@ constexpr int WIN = 256;      // kept candidates per staging window
 constexpr int CMAX = 1024;    // kept candidates per pass (bitmask length)
 constexpr int NWORD = CMAX / 32;
 constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the culling test
-constexpr int STG_SLOTS = (WIN / 2 * 16 + WIN * 16) / 2;  // 16-bit output slots in pw + f32
+constexpr int STG_BASE_SLOTS = (WIN / 2 * 16 + WIN * 16) / 2;  // 16-bit output slots in pw + f32
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
@@ -51,15 +51,16 @@ constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 constexpr int LOOKBACK_SPIN_LIMIT = 1 << 20;
 
 struct TileSmem {
-    // pw and f32 are contiguous: after the last window they hold the tile's
-    // staged output (16-bit kept-candidate slots), STG_SLOTS of them
-    uint4 pw[WIN / 2];  // FP16 pairs: word (g*16 + b) = kept candidates 32g + b (lo), 32g + 16 + b (hi)
-    float4 f32[WIN];    // FP32 frame coordinates, candidate index j in .w
     unsigned int S[TW][NWORD + 1];
     int jall[CMAX];            // kept candidates: sorted index
     unsigned char code[CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5
     int selfpos[TW];           // kept slot of each lane's own particle (-1: not in this fill)
     int rstart[9], rlen[9], rb[9][8];
+    // pw and f32 come last and are contiguous with any extra dynamic shared
+    // memory of the launch: after the last window they hold the tile's staged
+    // output (16-bit kept-candidate slots), stg_slots of them
+    uint4 pw[WIN / 2];  // FP16 pairs: word (g*16 + b) = kept candidates 32g + b (lo), 32g + 16 + b (hi)
+    float4 f32[WIN];    // FP32 frame coordinates, candidate index j in .w
 };
 
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
@@ -511,28 +512,33 @@ __device__ __forceinline__ void emit_bits(const TileSmem &S, int lane, int nw, l
     __syncwarp();
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__restrict__ tiles,
+// BATCH: tiles of several systems (td.w = system); each tile reads its
+// system's GridDev from gsys, g0 carries the shared status record and the
+// length of the concatenated sorted arrays.  Otherwise g0 is the grid.
+template <int DIM, bool BATCH>
+__global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g0, const GridDev *__restrict__ gsys,
+                                                 const int4 *__restrict__ tiles,
                                                  const long long *__restrict__ ntiles_dev,
                                                  long long *__restrict__ row_ptr, int *__restrict__ col,
                                                  long long cap, float *__restrict__ rho,
-                                                 unsigned long long *__restrict__ tstate) {
+                                                 unsigned long long *__restrict__ tstate, int stg_slots) {
     extern __shared__ __align__(16) unsigned char smraw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smraw);
     const int lane = threadIdx.x;
-    const int ny = g.nk[1];
     const bool want_rho = rho != nullptr;
     const long long ntiles = *ntiles_dev;
-    // culling threshold: T plus a margin for the FP16 coordinates it uses
-    const float cullT = __half2float(__hneg(__low2half(as_h2(g.neg_t16)))) + CULL_MARGIN;
     unsigned int n32 = 0, n64 = 0;
 
     while (true) {
         long long t = 0;
-        if (lane == 0) t = (long long)atomicAdd(&g.status->ticket, 1ull);
+        if (lane == 0) t = (long long)atomicAdd(&g0.status->ticket, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
         const int4 td = tiles[t];
+        const GridDev &g = BATCH ? gsys[td.w] : g0;
+        const int ny = g.nk[1];
+        // culling threshold: T plus a margin for the FP16 coordinates it uses
+        const float cullT = __half2float(__hneg(__low2half(as_h2(g.neg_t16)))) + CULL_MARGIN;
         const int p0 = td.x, cnt_home = td.y, row = td.z;
         const int cy = row % ny, cz = row / ny;
         const bool mine = lane < cnt_home;
@@ -571,17 +577,17 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__r
         // A simple tile whose row segment fits the staging area lays its
         // output out in shared memory before it needs its CSR offset, so the
         // wait on earlier tiles overlaps that work.
-        const bool staged = simple && col != nullptr && agg <= STG_SLOTS;
+        const bool staged = simple && col != nullptr && agg <= stg_slots;
         unsigned short *stg = reinterpret_cast<unsigned short *>(&S.pw[0]);
         if (staged) emit_bits(S, lane, mine ? (kept + 31) >> 5 : 0, rstart, stg, nullptr, nullptr);
-        const long long pre = look_back_resolve(tstate, t, agg, &g.status->flags);
+        const long long pre = look_back_resolve(tstate, t, agg, &g0.status->flags);
         const bool wc = col != nullptr && pre + agg <= cap;
-        if (col != nullptr && !wc && lane == 0) atomicOr(&g.status->flags, ST_CAPACITY);
+        if (col != nullptr && !wc && lane == 0) atomicOr(&g0.status->flags, ST_CAPACITY);
         if (mine) {
             row_ptr[h.i] = pre + rstart;
             if (want_rho) rho[h.i] = g.w_norm * (2.f / 3.f + acc);
         }
-        if (t == ntiles - 1 && lane == 0) row_ptr[g.n] = pre + agg;
+        if (t == ntiles - 1 && lane == 0) row_ptr[g0.n] = pre + agg;
         if (!wc) continue;
         if (staged) {
             // consecutive lanes on consecutive entries of the tile's segment
@@ -616,8 +622,8 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g, const int4 *__r
         n64 += __shfl_xor_sync(0xffffffffu, n64, o);
     }
     if (lane == 0) {
-        if (n32) atomicAdd(&g.status->fp32_pairs, (unsigned long long)n32);
-        if (n64) atomicAdd(&g.status->fp64_pairs, (unsigned long long)n64);
+        if (n32) atomicAdd(&g0.status->fp32_pairs, (unsigned long long)n32);
+        if (n64) atomicAdd(&g0.status->fp64_pairs, (unsigned long long)n64);
     }
 }
 
@@ -675,30 +681,43 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *
 
 // ntiles_dev: device pointer to the tile count (the last entry of the row
 // tile offsets); ntiles_max bounds it (sizes the look-back state).
-cudaError_t launch_nnps_tile(const GridDev &g, const int4 *tiles, const long long *ntiles_dev, long long ntiles_max,
-                             long long *row_ptr, int *col, long long cap, float *rho, unsigned long long *tstate,
-                             int sm_count, cudaStream_t s) {
-    const size_t sb = sizeof(TileSmem);
-    auto kern = g.dim == 2 ? k_nnps_tile<2> : k_nnps_tile<3>;
-    static bool attr_done[2] = {false, false};
-    if (!attr_done[g.dim - 2]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-        if (e != cudaSuccess) return e;
-        attr_done[g.dim - 2] = true;
-    }
+// gsys != nullptr: batch tiles (td.w = system), g then carries the status
+// record and the total particle count.  extra_smem: dynamic shared memory
+// beyond TileSmem, all of it staging area for the tile's output.
+cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
+                             long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
+                             unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s) {
+    const size_t sb = sizeof(TileSmem) + (size_t)extra_smem;
+    const bool batch = gsys != nullptr;
+    auto kern = g.dim == 2 ? (batch ? k_nnps_tile<2, true> : k_nnps_tile<2, false>)
+                           : (batch ? k_nnps_tile<3, true> : k_nnps_tile<3, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, sb);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)sm_count * per_sm;
     if (blocks > ntiles_max) blocks = ntiles_max;
     if (blocks < 1) blocks = 1;
-    cudaError_t e =
-        cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
+    e = cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    const int stg_slots = (int)((sizeof(TileSmem::pw) + sizeof(TileSmem::f32) + (size_t)extra_smem) / 2);
     ProfScope ps(TAG_FUSED, s);
     note_launch(1);
-    kern<<<(unsigned)blocks, 32, sb, s>>>(g, tiles, ntiles_dev, row_ptr, col, cap, rho, tstate);
+    kern<<<(unsigned)blocks, 32, sb, s>>>(g, gsys, tiles, ntiles_dev, row_ptr, col, cap, rho, tstate, stg_slots);
     return cudaGetLastError();
+}
+
+// Extra staging bytes for a grid whose rows hold about `nbr` neighbours on
+// average: enough for a tile of 32 such rows with 15% to spare, in
+// steps of 2 KB (each step costs occupancy), none when the window buffers
+// suffice.
+int tile_extra_smem(double nbr) {
+    const double want = 32.0 * nbr * 1.15 * 2.0;  // bytes of 16-bit slots
+    const double have = (double)(sizeof(TileSmem::pw) + sizeof(TileSmem::f32));
+    if (want <= have) return 0;
+    int extra = (int)((want - have + 2047.0) / 2048.0) * 2048;
+    return extra > 16384 ? 16384 : extra;
 }
 
 }  // namespace sph

@@ -11,6 +11,7 @@
 namespace sph {
 
 static std::atomic<long long> g_launches{0};
+static thread_local bool t_capturing = false;  // this thread is recording a CUDA graph
 static std::atomic<int> g_enabled{0};
 static std::mutex g_mu;
 
@@ -45,7 +46,7 @@ static cudaEvent_t take_event() {
 }
 
 ProfScope::ProfScope(int tag, cudaStream_t s) : tag_(tag), s_(s), a_(nullptr) {
-    if (!((g_enabled.load(std::memory_order_relaxed) >> tag) & 1)) return;
+    if (t_capturing || !((g_enabled.load(std::memory_order_relaxed) >> tag) & 1)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = take_event();
     cudaEventRecord((cudaEvent_t)a_, s_);
@@ -72,6 +73,8 @@ static void drain_locked() {
     g_pending.clear();
     cudaGetLastError();
 }
+
+void prof_set_capturing(bool on) { t_capturing = on; }
 
 void prof_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -42,6 +42,9 @@ class ProfScope {
 };
 
 void prof_enable(int on);
+// While a thread records a CUDA graph its ProfScopes record nothing (event
+// timing does not apply to captured work).
+void prof_set_capturing(bool on);
 // Enable timing for a comma-separated list of tag names only (NULL: all);
 // -1 if a name is unknown (nothing changed).
 int prof_select(const char *names);

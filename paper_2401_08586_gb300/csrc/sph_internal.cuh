@@ -89,6 +89,23 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double hc, int nk
     return (int)t;
 }
 
+// Cell index and cell-relative coordinate of one axis, in units of
+// u = h_c / 2 (Eq. 6 with the cell centre as reference):
+//   s = 2 (x - lo) / h_c,  c = clamp(floor(s / 2), 0, nk - 1),
+//   a = s - (2c + 1)  (exact: s and 2c + 1 are within one of each other).
+// Five FP64 operations and no division.  s carries a relative error of at
+// most 2^-52 (x - lo is exact whenever x and lo are within a factor of two),
+// i.e. at most 2^-31 u at the 2^20-cell limit, below the 2^-29 u margin that
+// the cell size kh (1 + 2^-30) leaves, so every pair closer than kh sits in
+// the same or adjacent cells.
+__device__ __forceinline__ int rel_axis(double x, double lo, double two_over_hc, int nk, double &a) {
+    const double s = __dmul_rn(__dsub_rn(x, lo), two_over_hc);
+    int c = __double2int_rd(s) >> 1;  // floor(floor(s) / 2) = floor(s / 2); saturating conversion
+    c = min(max(c, 0), nk - 1);
+    a = __dsub_rn(s, (double)(2 * c + 1));
+    return c;
+}
+
 // What another translation unit of the library may see of a grid
 // (filled by grid_view in api.cu).
 struct GridView {

@@ -55,6 +55,21 @@ class sph_grid_info(ctypes.Structure):
                 ("stat_fp32_pairs", ctypes.c_int64), ("stat_fp64_pairs", ctypes.c_int64)]
 
 
+class sph_batch_out(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("col_capacity", ctypes.c_int64),
+                ("rho", ctypes.c_void_p), ("orig_id", ctypes.c_void_p),
+                ("sys_first", ctypes.POINTER(ctypes.c_int64)), ("nnz", ctypes.c_int64)]
+
+
+class sph_batch_stats(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_int64), ("graph_captures", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("tuned_staging", ctypes.c_int32), ("tuned_candidates", ctypes.c_int32),
+                ("fp32_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64)]
+
+
+SPH_BATCH_OPT_GRAPH = 1
+SPH_BATCH_OPT_STAGING = 2
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -97,6 +112,12 @@ def load(build_if_missing=False):
         "sph_launch_count": [],
         "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
         "sph_nnps_query_static": [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp],
+        "sph_batch_run": [ctypes.POINTER(_vp), ctypes.POINTER(sph_params), ctypes.POINTER(_vp),
+                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(sph_batch_out), _vp],
+        "sph_batch_get_stats": [_vp, ctypes.POINTER(sph_batch_stats)],
+        "sph_batch_create": [ctypes.POINTER(_vp)],
+        "sph_batch_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
+        "sph_batch_free": [_vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +134,8 @@ def exported_symbols():
             "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
-            "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate"]
+            "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
+            "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free"]
 
 
 def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=None):
@@ -124,6 +146,7 @@ def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=Non
 
 
 SPH_OPT_FUSED = 1
+SPH_OPT_STAGING = 2
 
 
 def sph_grid_set_option(grid, option, value):
@@ -270,6 +293,113 @@ def _host_ptr(a):
 
 
 # ---- convenience ------------------------------------------------------------
+
+def sph_batch_run(batch, params_list, xyz_list, out, stream=None):
+    """One batched run.  batch: workspace handle (None on first use); params_list:
+    sph_params per system; xyz_list: (n_s, dim) float64 CUDA tensors; out: a
+    filled sph_batch_out.  Returns the (possibly new) workspace handle."""
+    nsys = len(params_list)
+    P = (sph_params * nsys)(*params_list)
+    X = (_vp * nsys)(*[_ptr(x) for x in xyz_list])
+    N = (ctypes.c_int64 * nsys)(*[int(x.shape[0]) for x in xyz_list])
+    h = _vp(batch)
+    _check(load().sph_batch_run(ctypes.byref(h), P, X, N, nsys, ctypes.byref(out), _stream(stream)))
+    return h.value
+
+
+def sph_batch_create():
+    h = _vp()
+    _check(load().sph_batch_create(ctypes.byref(h)))
+    return h.value
+
+
+def sph_batch_get_stats(batch):
+    st = sph_batch_stats()
+    _check(load().sph_batch_get_stats(batch, ctypes.byref(st)))
+    return st
+
+
+def sph_batch_set_option(batch, option, value):
+    _check(load().sph_batch_set_option(batch, int(option), int(value)))
+
+
+def sph_batch_free(batch):
+    _check(load().sph_batch_free(batch))
+
+
+class Batch:
+    """Workspace of batched runs plus torch-allocated outputs.
+
+    ``run(systems)`` takes a list of (xyz CUDA tensor, sph_params) and returns
+    (row_ptr, col, rho, orig_id, sys_first): the block-diagonal cell-order CSR
+    of the concatenation (see include/sph.h).  The output tensors are views of
+    buffers the workspace keeps and reuses (so a repeated run of the same
+    shapes replays its recorded CUDA graph); the next run overwrites them.
+    The column buffer grows, by a count-only run, when it is too small."""
+
+    def __init__(self):
+        self.handle = None
+        self.handle = sph_batch_create()
+        self._rp = self._col = self._rho = self._orig = None
+        self._first = None
+
+    def _buffers(self, ntot, nsys, dev, density):
+        import torch
+        if self._rp is None or self._rp.numel() != ntot + 1 or self._rp.device != dev:
+            self._rp = torch.empty(ntot + 1, dtype=torch.int64, device=dev)
+            self._orig = torch.empty(max(ntot, 1), dtype=torch.int32, device=dev)
+            self._rho = None
+        if density and self._rho is None:
+            self._rho = torch.empty(max(ntot, 1), dtype=torch.float32, device=dev)
+        if self._first is None or len(self._first) != nsys + 1:
+            self._first = (ctypes.c_int64 * (nsys + 1))()
+
+    def run(self, systems, density=True, stream=None, capacity=None):
+        import torch
+        xs = [x.contiguous() for x, _ in systems]
+        ps = [p for _, p in systems]
+        ntot = sum(int(x.shape[0]) for x in xs)
+        dev = xs[0].device
+        self._buffers(ntot, len(xs), dev, density)
+        rho = self._rho if density else None
+        if capacity is not None and (self._col is None or self._col.numel() < capacity):
+            self._col = torch.empty(max(int(capacity), 1), dtype=torch.int32, device=dev)
+        if self._col is None:
+            out = sph_batch_out(_ptr(self._rp), None, 0, None, _ptr(self._orig), self._first, 0)
+            sph_batch_run(self.handle, ps, xs, out, stream)
+            self._col = torch.empty(max(int(out.nnz * 1.05) + 1024, 1), dtype=torch.int32, device=dev)
+        while True:
+            out = sph_batch_out(_ptr(self._rp), _ptr(self._col), self._col.numel(), _ptr(rho), _ptr(self._orig),
+                                self._first, 0)
+            try:
+                sph_batch_run(self.handle, ps, xs, out, stream)
+                break
+            except SphError as e:
+                if e.code != SPH_ERR_CAPACITY:
+                    raise
+                self._col = torch.empty(int(out.nnz * 1.05) + 1024, dtype=torch.int32, device=dev)
+        self._keep = xs
+        nnz = int(out.nnz)
+        return (self._rp, self._col[:nnz], (rho[:ntot] if density else None), self._orig[:ntot],
+                list(self._first))
+
+    def stats(self):
+        return sph_batch_get_stats(self.handle)
+
+    def set_option(self, option, value):
+        sph_batch_set_option(self.handle, option, value)
+
+    def close(self):
+        if self.handle is not None:
+            sph_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 def make_params(dim, h, kh=None, order=SPH_ORDER_CELL, precision=SPH_PREC_FP16_RCLL, mass=1.0,
                 cell_size=0.0, box=None):
