@@ -319,13 +319,91 @@ int sph_batch_get_stats(sph_batch_t batch, sph_batch_stats *stats);
  * SPH_BATCH_OPT_STAGING: -1 (default) tune the tile search's staging bytes by
  *   timing 0, 2048, 4096 and 8192 on the first run of each density class
  *   (dimension and neighbours per particle to a quarter octave) and reuse the
- *   winner; 0 .. 65536 in multiples of 16 fix it. */
+ *   winner; -2 size it from the particle density without timing; 0 .. 65536
+ *   in multiples of 16 fix it. */
 #define SPH_BATCH_OPT_GRAPH 1
 #define SPH_BATCH_OPT_STAGING 2
 int sph_batch_set_option(sph_batch_t batch, int option, int64_t value);
 
 /* Free a workspace (synchronises the device).  NULL is a no-op. */
 int sph_batch_free(sph_batch_t batch);
+
+/* ---- Serving: a request server over the search ----------------------------
+ *
+ * A server owns worker threads (one CUDA stream each) on the device current
+ * at creation.  Clients submit particle systems; each request is binned,
+ * searched and its density summed, and its results stay in device memory
+ * owned by the server until the client releases them.  Admission keeps the
+ * device memory reserved for running requests plus held results within
+ * hbm_budget_bytes (each running request reserves an estimate for up to 128
+ * neighbours per particle in 3D, 40 in 2D; a finished one holds its exact
+ * result).  Requests start in submission order, except that younger requests
+ * that fit may pass one that does not, until it has waited max_wait_ns.
+ * Small cell-order requests (n <= small_n) waiting together of one dimension
+ * are searched as one batch (up to max_batch requests) and their results
+ * split afterwards (continuous batching).  A request that fails (for example
+ * a non-finite coordinate) reports its error alone; the others are unaffected.
+ * The paper serves no requests; this is the library's serving layer.
+ */
+typedef struct sph_server_s *sph_server_t;
+
+typedef struct {
+    int64_t hbm_budget_bytes; /* > 0 */
+    int32_t streams;          /* worker threads / CUDA streams, 0: 2 (max 16) */
+    int32_t max_batch;        /* requests per batched search, 0: 64 */
+    int64_t small_n;          /* batching threshold in particles, 0: 32768 */
+    int64_t max_wait_ns;      /* passing limit, 0: 20 ms */
+} sph_server_cfg;
+
+typedef struct {
+    sph_params params;      /* as for sph_bin_cells (order and precision are honoured) */
+    const double *xyz;      /* n x dim FP64; must stay valid and unchanged until the request completes */
+    int64_t n;
+    int32_t xyz_on_device;  /* 1: device pointer; 0: host pointer (copied when the request starts) */
+    int32_t want_density;   /* 1: compute rho */
+} sph_request;
+
+typedef struct {
+    int32_t status;            /* SPH_OK or the request's error code */
+    int64_t n, nnz;
+    const int64_t *row_ptr;    /* device int64[n + 1] (rows in the request's order: see params.order) */
+    const int32_t *col;        /* device int32[nnz] */
+    const float *rho;          /* device float[n] or NULL */
+    const int32_t *orig_id;    /* device int32[n] (cell order: sorted position -> input index) or NULL */
+    int64_t t_submit_ns, t_admit_ns, t_done_ns; /* steady clock: submitted, started, results ready */
+} sph_result;
+
+typedef struct {
+    int64_t submitted, completed, failed; /* requests */
+    int64_t batches, batched_requests;    /* batched searches and the requests they served */
+    int64_t held_bytes, peak_held_bytes;  /* reserved + held device bytes now / at most */
+    int64_t queued;                       /* requests waiting for admission */
+} sph_server_stats;
+
+/* Create a server (host call; starts the worker threads). */
+int sph_server_create(const sph_server_cfg *cfg, sph_server_t *server);
+/* Queue a request; *ticket identifies it.  SPH_ERR_INVALID for bad
+ * parameters, SPH_ERR_BUDGET when the request alone exceeds the budget. */
+int sph_serve_submit(sph_server_t server, const sph_request *req, uint64_t *ticket);
+/* SPH_PENDING while the request is queued or running; SPH_OK once it has
+ * finished (then *result is filled, result->status tells success or the
+ * request's error); SPH_ERR_NOT_FOUND for an unknown or released ticket. */
+int sph_serve_poll(sph_server_t server, uint64_t ticket, sph_result *result);
+/* As sph_serve_poll, waiting up to timeout_ns (< 0: without limit). */
+int sph_serve_wait(sph_server_t server, uint64_t ticket, int64_t timeout_ns, sph_result *result);
+/* Copy a finished request's results into caller buffers (device or host
+ * memory, any may be NULL; sizes n + 1, nnz, n, n) on `stream` (not
+ * synchronised).  SPH_ERR_INVALID before the request has finished, its own
+ * error code if it failed. */
+int sph_result_copy(sph_server_t server, uint64_t ticket, int64_t *row_ptr, int32_t *col, float *rho,
+                    int32_t *orig_id, void *stream);
+/* Free a finished request's device results; the ticket becomes unknown.
+ * The caller's own work on the result buffers must have completed. */
+int sph_result_release(sph_server_t server, uint64_t ticket);
+int sph_server_get_stats(sph_server_t server, sph_server_stats *stats);
+/* Stop the workers (running requests finish, queued ones are dropped), free
+ * every result and the server. */
+int sph_server_destroy(sph_server_t server);
 
 /* Per-kernel device timing of the library's own launches.  While enabled,
  * every launch is bracketed by CUDA events recorded on its stream.

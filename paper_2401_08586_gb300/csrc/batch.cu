@@ -222,7 +222,7 @@ struct sph_batch_s {
     GraphKey key;
     long long graph_launches = 0;  // kernels per replay
     bool use_graph = true;
-    int staging = -1;  // -1: autotune
+    int staging = -1;  // -1: autotune, -2: size from the density estimate without timing
     std::map<int, int> tuned;  // density class -> staging bytes
     sph_batch_stats stats;
 };
@@ -518,7 +518,9 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     const int dclass = dim * 1000 + (nbr > 0 ? (int)floor(4.0 * log2(nbr)) : -999);
     int extra = b->staging;
     bool tune = false;
-    if (extra < 0) {
+    if (extra == -2) {
+        extra = tile_extra_smem(nbr);
+    } else if (extra < 0) {
         auto it = b->tuned.find(dclass);
         if (it != b->tuned.end()) extra = it->second;
         else {
@@ -646,8 +648,8 @@ extern "C" int sph_batch_set_option(sph_batch_t batch, int option, int64_t value
         return SPH_OK;
     }
     if (option == SPH_BATCH_OPT_STAGING) {
-        if (value < -1 || value > 65536 || (value > 0 && value % 16 != 0))
-            return fail(SPH_ERR_INVALID, "SPH_BATCH_OPT_STAGING takes -1 or a multiple of 16 in [0, 65536]");
+        if (value < -2 || value > 65536 || (value > 0 && value % 16 != 0))
+            return fail(SPH_ERR_INVALID, "SPH_BATCH_OPT_STAGING takes -1, -2 or a multiple of 16 in [0, 65536]");
         batch->staging = (int)value;
         return SPH_OK;
     }

@@ -67,6 +67,29 @@ class sph_batch_stats(ctypes.Structure):
                 ("fp32_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64)]
 
 
+class sph_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("small_n", ctypes.c_int64), ("max_wait_ns", ctypes.c_int64)]
+
+
+class sph_request(ctypes.Structure):
+    _fields_ = [("params", sph_params), ("xyz", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("xyz_on_device", ctypes.c_int32), ("want_density", ctypes.c_int32)]
+
+
+class sph_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("orig_id", ctypes.c_void_p), ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class sph_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64), ("held_bytes", ctypes.c_int64),
+                ("peak_held_bytes", ctypes.c_int64), ("queued", ctypes.c_int64)]
+
+
 SPH_BATCH_OPT_GRAPH = 1
 SPH_BATCH_OPT_STAGING = 2
 
@@ -118,6 +141,14 @@ def load(build_if_missing=False):
         "sph_batch_create": [ctypes.POINTER(_vp)],
         "sph_batch_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
         "sph_batch_free": [_vp],
+        "sph_server_create": [ctypes.POINTER(sph_server_cfg), ctypes.POINTER(_vp)],
+        "sph_serve_submit": [_vp, ctypes.POINTER(sph_request), ctypes.POINTER(ctypes.c_uint64)],
+        "sph_serve_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(sph_result)],
+        "sph_serve_wait": [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(sph_result)],
+        "sph_result_copy": [_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp, _vp],
+        "sph_result_release": [_vp, ctypes.c_uint64],
+        "sph_server_get_stats": [_vp, ctypes.POINTER(sph_server_stats)],
+        "sph_server_destroy": [_vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -135,7 +166,9 @@ def exported_symbols():
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
-            "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free"]
+            "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
+            "sph_server_create", "sph_serve_submit", "sph_serve_poll", "sph_serve_wait", "sph_result_copy",
+            "sph_result_release", "sph_server_get_stats", "sph_server_destroy"]
 
 
 def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=None):
@@ -393,6 +426,119 @@ class Batch:
         if self.handle is not None:
             sph_batch_free(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sph_server_create(cfg):
+    h = _vp()
+    _check(load().sph_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def sph_serve_submit(server, req):
+    t = ctypes.c_uint64(0)
+    _check(load().sph_serve_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def sph_serve_poll(server, ticket):
+    """The finished request's sph_result, or None while it is pending."""
+    res = sph_result()
+    rc = load().sph_serve_poll(server, ticket, ctypes.byref(res))
+    if rc == SPH_PENDING:
+        return None
+    _check(rc)
+    return res
+
+
+def sph_serve_wait(server, ticket, timeout_ns=-1):
+    res = sph_result()
+    rc = load().sph_serve_wait(server, ticket, int(timeout_ns), ctypes.byref(res))
+    if rc == SPH_PENDING:
+        return None
+    _check(rc)
+    return res
+
+
+def sph_result_copy(server, ticket, row_ptr=None, col=None, rho=None, orig_id=None, stream=None):
+    _check(load().sph_result_copy(server, ticket, _ptr(row_ptr), _ptr(col), _ptr(rho), _ptr(orig_id),
+                                  _stream(stream)))
+
+
+def sph_result_release(server, ticket):
+    _check(load().sph_result_release(server, ticket))
+
+
+def sph_server_get_stats(server):
+    st = sph_server_stats()
+    _check(load().sph_server_get_stats(server, ctypes.byref(st)))
+    return st
+
+
+def sph_server_destroy(server):
+    _check(load().sph_server_destroy(server))
+
+
+class Server:
+    """Request server (see include/sph.h).  ``submit`` keeps a reference to
+    the coordinates until the request is released."""
+
+    def __init__(self, budget_bytes, streams=0, max_batch=0, small_n=0, max_wait_ns=0):
+        self.handle = None
+        self.handle = sph_server_create(sph_server_cfg(int(budget_bytes), streams, max_batch, small_n, max_wait_ns))
+        self._keep = {}
+
+    def submit(self, xyz, params, density=True):
+        """xyz: float64 array (numpy on the host, or a CUDA tensor)."""
+        if isinstance(xyz, np.ndarray):
+            xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+            ptr, on_dev = xyz.ctypes.data, 0
+        else:
+            xyz = xyz.contiguous()
+            ptr, on_dev = xyz.data_ptr(), 1
+        req = sph_request(params, ptr if xyz.shape[0] else None, int(xyz.shape[0]), on_dev, int(density))
+        t = sph_serve_submit(self.handle, req)
+        self._keep[t] = xyz
+        return t
+
+    def poll(self, ticket):
+        return sph_serve_poll(self.handle, ticket)
+
+    def wait(self, ticket, timeout_s=None):
+        return sph_serve_wait(self.handle, ticket, -1 if timeout_s is None else int(timeout_s * 1e9))
+
+    def fetch(self, ticket, stream=None):
+        """Copies of a finished request's results as CUDA tensors:
+        (row_ptr, col, rho or None, orig_id or None)."""
+        import torch
+        res = self.wait(ticket)
+        if res.status != SPH_OK:
+            raise SphError(res.status, "request %d failed" % ticket)
+        rp = torch.empty(res.n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(res.nnz, 1), dtype=torch.int32, device="cuda")
+        rho = torch.empty(max(res.n, 1), dtype=torch.float32, device="cuda") if res.rho else None
+        orig = torch.empty(max(res.n, 1), dtype=torch.int32, device="cuda") if res.orig_id else None
+        sph_result_copy(self.handle, ticket, rp, col, rho, orig, stream)
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return rp, col[:res.nnz], (rho[:res.n] if rho is not None else None), (orig[:res.n] if orig is not None else None)
+
+    def release(self, ticket):
+        sph_result_release(self.handle, ticket)
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        return sph_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            sph_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:
