@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["3d_1m", "2d_10k", "3d_8m"], default="3d_1m")
+    ap.add_argument("--workload", choices=["3d_1m", "2d_10k", "3d_8m", "batch_256", "serve"], default="3d_1m")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-CLL, e2e and CPU-baseline legs")
     ap.add_argument("--side", type=int, default=100,
@@ -171,9 +171,11 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    ps, desc = workload(args.workload)
     threads = os.cpu_count() or 1
     oracle.build.build()
+    if args.workload in ("batch_256", "serve"):
+        return run_reference_systems(args, threads)
+    ps, desc = workload(args.workload)
 
     def step():
         rp, col = oracle.cll(ps.xyz, ps.kh, threads=threads)
@@ -197,6 +199,44 @@ def run_reference(args, rank, world):
                          "sample": "full workload per step (FP64 cell link-list + density, OpenMP rows)"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_systems(args, threads):
+    """Reference arm of the batched and served workloads: the oracle over a
+    bounded sample of their systems (batched: the first systems in order;
+    served: the first requests, one after another, no queueing)."""
+    import numpy as np
+    import oracle
+    from paper_2401_08586_gb300 import workloads as W
+    if args.workload == "batch_256":
+        systems = W.c4_batched()
+        desc = BATCH_DESC
+    else:
+        systems = [W.materialise_request(sp) for _, sp, _ in W.c5_request_stream(count=40, materialise=False)]
+        desc = SERVE_DESC % (len(systems), 0)
+    per = []
+    for ps in systems:
+        t0 = time.perf_counter()
+        rp, col = oracle.cll(ps.xyz, ps.kh, threads=threads)
+        oracle.density(ps.xyz, ps.h, rp, col, threads=threads)
+        per.append((ps.n, time.perf_counter() - t0))
+        if sum(t for _, t in per) > 20.0:
+            break
+    parts = sum(n for n, _ in per)
+    tot = sum(t for _, t in per)
+    sample = "first %d of %d systems (%d particles), FP64 cell link-list + density" % (len(per), len(systems), parts)
+    if args.workload == "serve":
+        lat = np.array([1e3 * t for _, t in per])
+        value, unit, hib = float(np.percentile(lat, 99)), "ms", False
+    else:
+        value, unit, hib = parts / tot, "particles/s", True
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": len(per),
+            "warmup": 0, "ms_per_step": 1e3 * tot / len(per), "higher_is_better": hib, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -243,6 +283,10 @@ def main():
     from paper_2401_08586_gb300 import sph
 
     sph.load(build_if_missing=True)
+    if args.workload == "batch_256":
+        return bench_batch(args, sph, dev, world, rank, local)
+    if args.workload == "serve":
+        return bench_serve_line(args, sph, dev, world, rank, local)
     ps, desc = workload(args.workload)
     n = ps.n
     stream = torch.cuda.current_stream(dev)
@@ -366,6 +410,7 @@ def main():
             torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.MAX)
             line["e2e"]["value"] = world * n * args.steps / float(e.item())
         line["e2e"].pop("seconds", None)
+        line["serving"] = bench_serve(sph, dev, count=450, warm=50)
         if world == 1 and rank == 0:
             line["cpu_baseline"] = cpu_baseline(ps)
     sph.sph_grid_free(grid)
@@ -432,6 +477,221 @@ def bench_e2e(sph, ps, dev, stream, args):
     sph.sph_grid_free(g)
     return {"value": n * args.steps / t, "unit": "particles/s", "h2d_bytes_per_step": n * ps.dim * 8,
             "d2h_bytes_per_step": n * 4 + 8, "seconds": t}
+
+
+SERVE_DESC = ("serve: Poisson arrivals at 200 req/s, 70%% 3D / 30%% 2D, N log-uniform in [1e3, 2e6], jittered "
+              "lattices dx = 1/ceil(N^(1/d)), h/dx U[1.2, 1.5], kh = 2h, 64 GB budget, 2 worker streams, seed 5; "
+              "%d timed requests after %d warm-up")
+
+
+def device_request(spec, dev):
+    """One request's coordinates drawn on the device (the lattice recipe of
+    the request stream, jitter from torch's generator seeded by the request)."""
+    import torch
+    dim, n = spec["dim"], spec["n"]
+    side = int(math.ceil(n ** (1.0 / dim)))
+    dx = 1.0 / side
+    idx = torch.arange(n, device=dev, dtype=torch.int64)
+    cols = []
+    for k in range(dim):
+        cols.append(((idx // side ** k) % side).to(torch.float64).add_(0.5).mul_(dx))
+    xyz = torch.stack(cols, 1)
+    g = torch.Generator(device=dev)
+    g.manual_seed(spec["seed"] % (1 << 62))
+    xyz += (torch.rand(xyz.shape, generator=g, device=dev, dtype=torch.float64) * 2 - 1) * (0.1 * dx)
+    return xyz.contiguous(), spec["hr"] * dx
+
+
+def bench_serve(sph, dev, count=2000, warm=200, rate=200.0):
+    """Replay the request stream against a server; latencies of the requests
+    after the warm-up.  Results stay on the device until each is released;
+    the D2H figure adds each result's copy to pinned host memory."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_2401_08586_gb300 import workloads as W
+    specs = W.c5_request_stream(count=count + warm, rate=rate, materialise=False)
+    reqs = [device_request(sp, dev) for _, sp, _ in specs]
+    torch.cuda.synchronize()
+    srv = sph.Server(64 << 30, streams=2)
+    tickets = [None] * len(specs)
+    done = {}
+    d2h_s = {}
+    pin_col = torch.empty(2_000_000 * 130, dtype=torch.int32).pin_memory()
+    pin_rp = torch.empty(2_000_001, dtype=torch.int64).pin_memory()
+    pin_rho = torch.empty(2_000_000, dtype=torch.float32).pin_memory()
+    copy_stream = torch.cuda.Stream(dev)
+    ready = threading.Event()
+    failed = {}
+
+    def completer():
+        for k in range(len(specs)):
+            while tickets[k] is None:
+                ready.wait(0.001)
+            res = srv.wait(tickets[k])
+            if res.status != sph.SPH_OK:
+                failed[k] = "%d: %s" % (res.status, sph.sph_last_error())
+                srv.release(tickets[k])
+                continue
+            t0 = time.perf_counter()
+            sph.sph_result_copy(srv.handle, tickets[k], pin_rp, pin_col, pin_rho, None, copy_stream)
+            copy_stream.synchronize()
+            d2h_s[k] = time.perf_counter() - t0
+            done[k] = (res.t_submit_ns, res.t_admit_ns, res.t_done_ns, res.n)
+            srv.release(tickets[k])
+
+    th = threading.Thread(target=completer)
+    th.start()
+    t_start = time.perf_counter()
+    for k, (t_arr, sp, _) in enumerate(specs):
+        now = time.perf_counter() - t_start
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        xyz, h = reqs[k]
+        tickets[k] = srv.submit(xyz, sph.make_params(sp["dim"], h, 2 * h, order=sph.SPH_ORDER_CELL))
+        ready.set()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    if failed:
+        raise RuntimeError("%d requests failed, first: %s" % (len(failed), next(iter(failed.items()))))
+    ks = range(warm, len(specs))
+    lat = np.array([(done[k][2] - done[k][0]) / 1e6 for k in ks])
+    lat_d2h = np.array([(done[k][2] - done[k][0]) / 1e6 + 1e3 * d2h_s[k] for k in ks])
+    queue = np.array([(done[k][1] - done[k][0]) / 1e6 for k in ks])
+    parts = sum(done[k][3] for k in ks)
+    span_s = (max(done[k][2] for k in ks) - min(done[k][0] for k in ks)) / 1e9
+    return {"requests": count, "warmup": warm, "rate_per_s": rate,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p99_with_d2h_ms": float(np.percentile(lat_d2h, 99)), "mean_ms": float(lat.mean()),
+            "p99_queue_ms": float(np.percentile(queue, 99)), "particles_per_s": parts / span_s,
+            "batches": int(st.batches), "batched_requests": int(st.batched_requests),
+            "peak_held_gb": st.peak_held_bytes / 2 ** 30}
+
+
+def bench_serve_line(args, sph, dev, world, rank, local):
+    count = args.steps if args.steps != 100 else 2000
+    with ClockSampler(local) as clk:
+        r = bench_serve(sph, dev, count=count, warm=200)
+    line = {"metric": METRIC, "value": r["p99_ms"], "unit": "ms", "n_gpus": world, "steps": count,
+            "warmup": 200, "ms_per_step": r["mean_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": SERVE_DESC % (count, 200), "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clk.summary(), "serving": r}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+BATCH_DESC = ("batch_256: 256 independent 3D jittered lattices, N log-uniform in [2e3, 2e5], dx U[0.005, 0.02], "
+              "h/dx U[1.2, 1.5], kh = 2h, jitter U(+-0.1dx), seed 4")
+
+
+def bench_batch(args, sph, dev, world, rank, local):
+    """The batched workload through sph_batch_run: one step = one run over all
+    256 systems (bounds, binning, tile search with fused density, nnz read)."""
+    import torch
+    from paper_2401_08586_gb300 import workloads as W
+    systems = W.c4_batched()
+    xs = [torch.from_numpy(ps.xyz).to(dev) for ps in systems]
+    params = [sph.make_params(3, ps.h, ps.kh, order=sph.SPH_ORDER_CELL) for ps in systems]
+    ntot = sum(ps.n for ps in systems)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    b = sph.Batch()
+    pairs = list(zip(xs, params))
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        b.run(pairs, stream=stream)
+    torch.cuda.synchronize()
+    st0 = b.stats()
+    sph.sph_profile_reset()
+    sph.sph_profile_select("fused")
+    launches0 = sph.sph_launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            rp, col, rho, orig, first = b.run(pairs, stream=stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+    launches = sph.sph_launch_count() - launches0
+    sph.sph_profile_enable(False)
+    ms, c = sph.sph_profile_read("fused")
+    st = b.stats()
+    total_s = sum(a.elapsed_time(e) for a, e in evs) / 1e3
+    nnz = int(rp[-1].item())
+    value = world * ntot * args.steps / total_s
+    dom_ms = ms / max(c, 1)
+    alg = ntot * (8 + 16 + 8 + 4) + 4 * nnz
+    peak, peak_src = measured_peaks()
+    achieved = alg / (dom_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": BATCH_DESC, "n_particles": ntot, "systems": len(systems), "dim": 3, "order": "cell",
+                   "density": "fused, fp32 accumulation", "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "clocks": clk.summary(), "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "k_nnps_tile (batch)", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "launch_ms": dom_ms,
+                     "algorithmic_bytes_per_launch": alg, "traffic": None},
+        "nnz": nnz, "neighbours_per_particle": nnz / ntot, "wall_s_timed": t1 - t0,
+        "batch": {"graph_replays_timed": st.graph_replays - st0.graph_replays, "graph_captures": st.graph_captures,
+                  "tuned_staging_bytes": st.tuned_staging, "fp32_pairs": st.fp32_pairs, "fp64_pairs": st.fp64_pairs},
+    }
+    if not args.no_extras:
+        # end to end: pinned host coordinates in, densities and nnz out, every step
+        xh = [torch.from_numpy(ps.xyz).pin_memory() for ps in systems]
+        rho_h = torch.empty(ntot, dtype=torch.float32).pin_memory()
+        xd = [torch.empty_like(x) for x in xs]
+        pd = list(zip(xd, params))
+        for x, h in zip(xd, xh):
+            x.copy_(h, non_blocking=True)
+        b.run(pd, stream=stream)
+        torch.cuda.synchronize()
+        t = 0.0
+        for k in range(args.steps):
+            ta = time.perf_counter()
+            for x, h in zip(xd, xh):
+                x.copy_(h, non_blocking=True)
+            rp, col, rho, orig, first = b.run(pd, stream=stream)
+            rho_h.copy_(rho, non_blocking=True)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - ta
+        line["e2e"] = {"value": ntot * args.steps / t, "unit": "particles/s", "h2d_bytes_per_step": ntot * 3 * 8,
+                       "d2h_bytes_per_step": ntot * 4 + 8}
+        if world == 1 and rank == 0:
+            line["cpu_baseline"] = cpu_baseline_systems(systems)
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_systems(systems, budget_s=12.0):
+    """The oracle on all host cores over the batch's systems in order, until
+    about budget_s has passed (a bounded sample of the workload)."""
+    import oracle
+    oracle.build.build()
+    threads = os.cpu_count() or 1
+    done, t = 0, 0.0
+    k = 0
+    while t < budget_s and k < len(systems):
+        ps = systems[k]
+        t0 = time.perf_counter()
+        rp, col = oracle.cll(ps.xyz, ps.kh, threads=threads)
+        oracle.density(ps.xyz, ps.h, rp, col, threads=threads)
+        t += time.perf_counter() - t0
+        done += ps.n
+        k += 1
+    return {"value": done / t, "unit": "particles/s", "cores": threads, "kind": "oracle",
+            "sample": "first %d of %d systems (%d particles), FP64 cell link-list + density" % (k, len(systems), done)}
 
 
 if __name__ == "__main__":

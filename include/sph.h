@@ -313,9 +313,10 @@ typedef struct {
 } sph_batch_stats;
 int sph_batch_get_stats(sph_batch_t batch, sph_batch_stats *stats);
 
-/* SPH_BATCH_OPT_GRAPH: 1 (default) record the launch sequence after the
- *   bounds as a CUDA graph and replay it while the batch's sizes and buffers
- *   are unchanged; 0 launch directly every time.
+/* SPH_BATCH_OPT_GRAPH: 1 (default) record the binning and tile-list launches
+ *   (after the bounds, before the search) as a CUDA graph and replay it while
+ *   the batch's sizes and buffers are unchanged; 0 launch directly every time.
+ *   The search is one direct launch either way.
  * SPH_BATCH_OPT_STAGING: -1 (default) tune the tile search's staging bytes by
  *   timing 0, 2048, 4096 and 8192 on the first run of each density class
  *   (dimension and neighbours per particle to a quarter octave) and reuse the

@@ -11,10 +11,11 @@
 // kernel reads from a device table), so the output is one block-diagonal
 // CSR over the concatenation.
 //
-// After the bounds (one device->host read for all systems), the launch
-// sequence depends only on the batch's shapes and buffers: it is recorded
-// once as a CUDA graph and replayed while they stay the same.  The staging
-// size of the tile search is tuned by timing the candidates on the first run
+// After the bounds (one device->host read for all systems), the launches of
+// the binning and tile-list steps depend only on the batch's shapes and
+// buffers: they are recorded once as a CUDA graph and replayed while those
+// stay the same.  The tile search itself is one persistent launch after the
+// graph; its staging size is tuned by timing the candidates on the first run
 // of each density class.
 #include <math.h>
 #include <string.h>
@@ -194,7 +195,7 @@ unsigned grid_blocks(long long n, int nt, int sm_count, int per_sm) {
 // Everything the recorded launch sequence depends on besides table contents.
 struct GraphKey {
     long long ntot, ncell, nrow, ntiles_max, cap;
-    int nsys, dim, extra;
+    int nsys, dim;
     const void *ptrs[32];
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
@@ -278,10 +279,10 @@ static int batch_create(sph_batch_s **out) {
     return SPH_OK;
 }
 
-// Launches after the bounds: binning of all systems, tile list, search.
-static cudaError_t batch_sequence(sph_batch_s *b, int nsys, int dim, long long ntot, long long ncell,
-                                  long long nrow, long long ntiles_max, const sph_batch_out *out, int extra,
-                                  cudaStream_t s) {
+// Launches after the bounds up to the search: binning of all systems and the
+// tile list (the part recorded as a CUDA graph).
+static cudaError_t batch_prep(sph_batch_s *b, int nsys, int dim, long long ntot, long long ncell, long long nrow,
+                              const sph_batch_out *out, cudaStream_t s) {
     const int nt = 256;
     const BinSys *bsys = P<BinSys>(b->bsys);
     const long long *first = P<long long>(b->first), *row_first = P<long long>(b->row_first);
@@ -323,11 +324,17 @@ static cudaError_t batch_sequence(sph_batch_s *b, int nsys, int dim, long long n
         k_batch_rows_write<<<rb, nt, 0, s>>>(bsys, row_first, nsys, nrow, P<int>(b->cell_start),
                                              P<long long>(b->toff), P<int4>(b->tiles));
     }
+    return cudaGetLastError();
+}
+
+// The tile search over all systems' tiles (one persistent launch).
+static cudaError_t batch_search(sph_batch_s *b, int dim, long long ntot, long long nrow, long long ntiles_max,
+                                const sph_batch_out *out, int extra, cudaStream_t s) {
     GridDev g0;
     memset(&g0, 0, sizeof(g0));
     g0.dim = dim;
     g0.n = (int)ntot;
-    g0.status = st;
+    g0.status = P<DevStatus>(b->status);
     return launch_nnps_tile(g0, P<GridDev>(b->gsys), P<int4>(b->tiles), P<long long>(b->toff) + nrow, ntiles_max,
                             reinterpret_cast<long long *>(out->row_ptr), out->col, out->col ? out->col_capacity : 0,
                             out->rho, P<unsigned long long>(b->tstate), extra, b->sm_count, s);
@@ -340,17 +347,9 @@ static float time_search(sph_batch_s *b, int dim, long long ntot, long long nrow
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    GridDev g0;
-    memset(&g0, 0, sizeof(g0));
-    g0.dim = dim;
-    g0.n = (int)ntot;
-    g0.status = P<DevStatus>(b->status);
-    launch_status_reset_counters(g0.status, s);
+    launch_status_reset_counters(P<DevStatus>(b->status), s);
     cudaEventRecord(e0, s);
-    cudaError_t err = launch_nnps_tile(g0, P<GridDev>(b->gsys), P<int4>(b->tiles), P<long long>(b->toff) + nrow,
-                                       ntiles_max, reinterpret_cast<long long *>(out->row_ptr), out->col,
-                                       out->col ? out->col_capacity : 0, out->rho, P<unsigned long long>(b->tstate),
-                                       extra, b->sm_count, s);
+    cudaError_t err = batch_search(b, dim, ntot, nrow, ntiles_max, out, extra, s);
     cudaEventRecord(e1, s);
     float ms = INFINITY;
     if (err == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
@@ -539,7 +538,6 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     key.cap = out->col ? out->col_capacity : 0;
     key.nsys = nsys;
     key.dim = dim;
-    key.extra = extra;
     const void *ptrs[] = {out->row_ptr, out->col, out->rho, out->orig_id, b->bsys.p, b->gsys.p, b->first.p,
                           b->row_first.p, b->status.p, b->cnt.p, b->cid.p, b->slot.p, b->cell_start.p,
                           b->orig_g.p, b->orig_l.p, b->rank.p, b->scell_x.p, b->rel16u.p, b->rel32u.p,
@@ -551,17 +549,51 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     b->stats.runs++;
     if (ntot == 0) {
         SPH_CUDA(cudaMemsetAsync(out->row_ptr, 0, sizeof(int64_t), s));
-    } else if (b->use_graph && !tune && b->exec && b->key == key) {
-        SPH_CUDA(cudaGraphLaunch(b->exec, s));
-        note_launch((int)b->graph_launches);
-        b->stats.graph_replays++;
     } else {
-        // direct launches (always when tuning: the candidates are timed here)
-        cudaError_t e = batch_sequence(b, nsys, dim, ntot, ncell, nrow, ntiles_max, out, extra, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(SPH_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+        // binning and tile list: the replayed graph, or direct launches
+        // (recorded for the next run unless the graph is switched off)
+        if (b->use_graph && b->exec && b->key == key) {
+            SPH_CUDA(cudaGraphLaunch(b->exec, s));
+            note_launch((int)b->graph_launches);
+            b->stats.graph_replays++;
+        } else {
+            cudaError_t e = batch_prep(b, nsys, dim, ntot, ncell, nrow, out, s);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(SPH_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+            }
+            if (b->use_graph) {
+                if (b->exec) {
+                    cudaGraphExecDestroy(b->exec);
+                    b->exec = nullptr;
+                }
+                cudaGraph_t graph = nullptr;
+                const long long l0 = launch_count();
+                prof_set_capturing(true);
+                cudaError_t ce = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
+                if (ce == cudaSuccess) {
+                    ce = batch_prep(b, nsys, dim, ntot, ncell, nrow, out, b->cap_stream);
+                    cudaError_t ce2 = cudaStreamEndCapture(b->cap_stream, &graph);
+                    if (ce == cudaSuccess) ce = ce2;
+                }
+                prof_set_capturing(false);
+                // captured work does not run: take the recorded launches back
+                // out of the launch count; each replay adds them
+                b->graph_launches = launch_count() - l0;
+                note_launch(-(int)b->graph_launches);
+                if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (ce != cudaSuccess) {
+                    cudaGetLastError();
+                    b->exec = nullptr;
+                } else {
+                    b->key = key;
+                    b->stats.graph_captures++;
+                }
+            }
         }
+        // the search: tuned candidates are timed here (each run leaves the
+        // same result), then one launch with the chosen staging
         if (tune) {
             const int cand[] = {0, 2048, 4096, 8192};
             float best_ms = INFINITY;
@@ -577,38 +609,9 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
             b->stats.tuned_staging = best;
             b->stats.tuned_candidates = (int)(sizeof(cand) / sizeof(cand[0]));
             extra = best;
-            key.extra = best;
         }
-        if (b->use_graph) {
-            // record the sequence for the next run with the same key
-            if (b->exec) {
-                cudaGraphExecDestroy(b->exec);
-                b->exec = nullptr;
-            }
-            cudaGraph_t graph = nullptr;
-            const long long l0 = launch_count();
-            prof_set_capturing(true);
-            cudaError_t ce = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
-            if (ce == cudaSuccess) {
-                ce = batch_sequence(b, nsys, dim, ntot, ncell, nrow, ntiles_max, out, extra, b->cap_stream);
-                cudaError_t ce2 = cudaStreamEndCapture(b->cap_stream, &graph);
-                if (ce == cudaSuccess) ce = ce2;
-            }
-            prof_set_capturing(false);
-            // captured work does not run: take the recorded launches back out
-            // of the launch count; each replay adds them
-            b->graph_launches = launch_count() - l0;
-            note_launch(-(int)b->graph_launches);
-            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            if (ce != cudaSuccess) {
-                cudaGetLastError();
-                b->exec = nullptr;
-            } else {
-                b->key = key;
-                b->stats.graph_captures++;
-            }
-        }
+        SPH_CUDA(launch_status_reset_counters(P<DevStatus>(b->status), s));
+        SPH_CUDA(batch_search(b, dim, ntot, nrow, ntiles_max, out, extra, s));
     }
 
     // ---- nnz, status ------------------------------------------------------------

@@ -18,6 +18,8 @@
 //      CSR offset, and write row_ptr, rho and the staged columns (coalesced).
 // Larger cells fall back to the general path (nnps_common.cuh): a counting
 // sweep before the look-back and a writing sweep after it.
+#include <mutex>
+
 #include "nnps_common.cuh"
 
 namespace sph {
@@ -298,12 +300,12 @@ cudaError_t launch_fused_t(const GridDev &g, long long *row_ptr, int *col, long 
     auto kern = k_nnps_fused<DIM>;
     const size_t sb = sizeof(FastSmem) > sizeof(SmemGen<SPH_PREC_FP16_RCLL>) ? sizeof(FastSmem)
                                                                             : sizeof(SmemGen<SPH_PREC_FP16_RCLL>);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static std::once_flag once;
+    static cudaError_t once_err = cudaSuccess;
+    std::call_once(once, [&] {
+        once_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    });
+    if (once_err != cudaSuccess) return once_err;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTF, sb);
     if (per_sm < 1) per_sm = 1;

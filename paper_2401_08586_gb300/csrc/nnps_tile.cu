@@ -29,6 +29,8 @@
 // and density, and emits its row from the kept bits.  Tiles with several
 // home groups or more than CMAX kept candidates run the steps twice (count,
 // then emit straight to their rows after the look-back).
+#include <mutex>
+
 #include "nnps_common.cuh"
 
 namespace sph {
@@ -43,6 +45,7 @@ constexpr int WIN = 256;      // kept candidates per staging window
 constexpr int CMAX = 1024;    // kept candidates per pass (bitmask length)
 constexpr int NWORD = CMAX / 32;
 constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the culling test
+constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch may ask for
 constexpr int STG_BASE_SLOTS = (WIN / 2 * 16 + WIN * 16) / 2;  // 16-bit output slots in pw + f32
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
@@ -687,12 +690,23 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
                              unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s) {
+    if (extra_smem < 0 || extra_smem > TILE_MAX_EXTRA_SMEM) return cudaErrorInvalidValue;
     const size_t sb = sizeof(TileSmem) + (size_t)extra_smem;
     const bool batch = gsys != nullptr;
-    auto kern = g.dim == 2 ? (batch ? k_nnps_tile<2, true> : k_nnps_tile<2, false>)
-                           : (batch ? k_nnps_tile<3, true> : k_nnps_tile<3, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    if (e != cudaSuccess) return e;
+    const int ki = (g.dim == 2 ? 0 : 2) + (batch ? 1 : 0);
+    auto kern = ki == 0 ? k_nnps_tile<2, false> : ki == 1 ? k_nnps_tile<2, true>
+              : ki == 2 ? k_nnps_tile<3, false> : k_nnps_tile<3, true>;
+    // The shared-memory limit is set once per kernel, to the largest launch
+    // any option allows (launches from several threads then never see a
+    // limit another thread lowered).
+    static std::once_flag once[4];
+    static cudaError_t once_err[4];
+    std::call_once(once[ki], [&] {
+        once_err[ki] = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(TileSmem) + TILE_MAX_EXTRA_SMEM));
+    });
+    if (once_err[ki] != cudaSuccess) return once_err[ki];
+    cudaError_t e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, sb);
     if (per_sm < 1) per_sm = 1;

@@ -2,6 +2,8 @@
 // (count pass, row scan, fill pass), the unfused density over an existing
 // CSR, and the canonical-order assembly.  The per-cell search itself is in
 // nnps_common.cuh; the single-pass fused search is in nnps_fused.cu.
+#include <mutex>
+
 #include "nnps_common.cuh"
 
 namespace sph {
@@ -115,12 +117,12 @@ static cudaError_t launch_nnps_t(const GridDev &g, int *cnt, const long long *ro
                                  long long cap, float *rho, int sm_count, cudaStream_t s) {
     auto kern = k_nnps<DIM, PREC, MODE>;
     const size_t sb = smem_bytes<PREC>();
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static std::once_flag once;
+    static cudaError_t once_err = cudaSuccess;
+    std::call_once(once, [&] {
+        once_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    });
+    if (once_err != cudaSuccess) return once_err;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sb);
     if (per_sm < 1) per_sm = 1;
