@@ -158,10 +158,8 @@ class ClockSampler:
 
 
 def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2401_08586_gb300 import replicas
+    return replicas.rank_env()
 
 
 # ----------------------------------------------------------------- reference arm
@@ -274,10 +272,10 @@ def main():
 
     import numpy as np
     import torch
+    from paper_2401_08586_gb300 import replicas
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        replicas.init("nccl", world)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     from paper_2401_08586_gb300 import sph
@@ -315,8 +313,7 @@ def main():
     sph.sph_grid_check(grid, sptr)
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier(world)
         torch.cuda.synchronize()
 
     # timed region: CUDA events around the search kernel only (the roofline's
@@ -339,11 +336,7 @@ def main():
     sph.sph_profile_enable(False)
     sph.sph_grid_check(grid, sptr)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    dev_total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([dev_total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_total_s = float(t.item())
+    dev_total_s = replicas.max_over_ranks(sum(step_ms) / 1e3, world, dev)
     value = world * n * args.steps / dev_total_s
     timed = {}
     for tag in ("fused", "fill"):
@@ -406,9 +399,8 @@ def main():
         line["fp64_cll"]["device_fp64_fma_tflops"] = sph.sph_device_fp64_rate() / 1e12
         line["e2e"] = bench_e2e(sph, ps, dev, stream, args)
         if world > 1:
-            e = torch.tensor([line["e2e"]["seconds"]], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.MAX)
-            line["e2e"]["value"] = world * n * args.steps / float(e.item())
+            line["e2e"]["value"] = world * n * args.steps / replicas.max_over_ranks(line["e2e"]["seconds"], world,
+                                                                                    dev)
         line["e2e"].pop("seconds", None)
         line["serving"] = bench_serve(sph, dev, count=450, warm=50)
         if world == 1 and rank == 0:
@@ -416,8 +408,7 @@ def main():
     sph.sph_grid_free(grid)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    replicas.finish(world)
     return 0
 
 
@@ -591,8 +582,10 @@ def bench_batch(args, sph, dev, world, rank, local):
     """The batched workload through sph_batch_run: one step = one run over all
     256 systems (bounds, binning, tile search with fused density, nnz read)."""
     import torch
+    from paper_2401_08586_gb300 import replicas
     from paper_2401_08586_gb300 import workloads as W
-    systems = W.c4_batched()
+    all_systems = W.c4_batched()
+    systems = replicas.shard(all_systems, world, rank)  # independent systems: round-robin over the ranks
     xs = [torch.from_numpy(ps.xyz).to(dev) for ps in systems]
     params = [sph.make_params(3, ps.h, ps.kh, order=sph.SPH_ORDER_CELL) for ps in systems]
     ntot = sum(ps.n for ps in systems)
@@ -610,6 +603,7 @@ def bench_batch(args, sph, dev, world, rank, local):
     launches0 = sph.sph_launch_count()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
+        replicas.barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.steps):
@@ -618,6 +612,7 @@ def bench_batch(args, sph, dev, world, rank, local):
             rp, col, rho, orig, first = b.run(pairs, stream=stream)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
+        replicas.barrier(world)
         t1 = time.perf_counter()
     launches = sph.sph_launch_count() - launches0
     sph.sph_profile_enable(False)
@@ -625,7 +620,7 @@ def bench_batch(args, sph, dev, world, rank, local):
     st = b.stats()
     total_s = sum(a.elapsed_time(e) for a, e in evs) / 1e3
     nnz = int(rp[-1].item())
-    value = world * ntot * args.steps / total_s
+    value = replicas.whole_job_rate(ntot * args.steps, total_s, world, dev)
     dom_ms = ms / max(c, 1)
     alg = ntot * (8 + 16 + 8 + 4) + 4 * nnz
     peak, peak_src = measured_peaks()
@@ -634,7 +629,8 @@ def bench_batch(args, sph, dev, world, rank, local):
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": BATCH_DESC, "n_particles": ntot, "systems": len(systems), "dim": 3, "order": "cell",
+        "config": {"workload": BATCH_DESC, "n_particles": int(replicas.sum_over_ranks(ntot, world, dev)),
+                   "systems": len(all_systems), "dim": 3, "order": "cell",
                    "density": "fused, fp32 accumulation", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "clocks": clk.summary(), "gpu_launches": launches,
@@ -671,6 +667,7 @@ def bench_batch(args, sph, dev, world, rank, local):
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+    replicas.finish(world)
     return 0
 
 
