@@ -257,6 +257,27 @@ int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, floa
 int sph_grid_csr(sph_grid_t grid, const int64_t **row_ptr, const int32_t **col, const float **rho,
                  int64_t *nnz);
 
+/* Mixed-precision time step (Eq. 8-9): advance a binned FP16-RCLL grid by
+ * one step of its particles' motion without converting the absolute
+ * coordinates again.  The cell-relative coordinates move by 2 v dt / h_c
+ * (Eq. 8, displacement v dt of Eq. 9, kept in FP64 and rounded once to
+ * FP16 / FP32 as binning rounds them); a particle whose coordinate leaves
+ * [-1, 1] moves to the adjacent cell; the cell order is then rebuilt from the
+ * integer cell ids (no bounds pass).  The grid's box is kept: if a particle
+ * leaves it the grid is binned again from xyz_new (with a caller box that is
+ * SPH_ERR_INVALID instead).
+ *   xyz_new  device FP64 n x dim (input order): the positions after the step,
+ *            x + v dt as the caller computes them.  FP64 decisions use them
+ *            from now on; the array must stay valid like sph_bin_cells' xyz.
+ *   vel      device FP64 n x dim (input order), dt the step.
+ * The FP64 relative coordinates accumulate rounding apart from xyz_new; the
+ * library bounds that drift each step and derives them again from the
+ * positions before it could reach 1e-7 u (u = h_c / 2), far inside the bands,
+ * so the neighbour lists stay those of the FP64 definition on xyz_new.
+ * Other grids (FP64-CLL, n == 0) are binned again from xyz_new.
+ * Synchronises `stream` once.  SPH_ERR_INVALID for non-finite velocities. */
+int sph_advance(sph_grid_t grid, const double *xyz_new, const double *vel, double dt, void *stream);
+
 /* ---- Batched runs: many independent systems in one pass ----------------------
  *
  * sph_batch_run bins, searches and sums the density of nsys independent

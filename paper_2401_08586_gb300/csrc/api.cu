@@ -34,6 +34,9 @@ struct sph_grid_s {
     int fused_enabled = 1;  // search variant for cell-order FP16 queries (SPH_OPT_FUSED)
     int staging = -1;       // extra staging bytes of the tile search (SPH_OPT_STAGING; -1: automatic)
     double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
+    DevBuf rel64, rel64u;   // FP64 relative coordinates kept across time steps (cell / input order)
+    bool rel64_valid = false;
+    double drift = 0;       // bound on |rel64 - conversion of xyz| in units of u
     long long own_nnz = 0;
     DevStatus *h_status = nullptr;  // pinned host mirror
 };
@@ -111,6 +114,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
     g->n = n;
     g->xyz = xyz;
     g->hc = p->cell_size != 0 ? p->cell_size : p->kh * (1.0 + 0x1p-30);
+    g->rel64_valid = false;
     const int dim = p->dim;
     int rc = SPH_OK;
     do {
@@ -200,6 +204,64 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
         *grid = nullptr;
     }
     return rc;
+}
+
+// Largest drift of the FP64 relative coordinates from the caller's positions
+// (units of u) that the search's bands absorb: the FP32 band keeps 2.5e-6 u^2
+// of slack over its worst case, and a drift d moves r^2 by at most ~14 d.
+static const double DRIFT_BUDGET = 1e-7;
+
+extern "C" int sph_advance(sph_grid_t grid, const double *xyz_new, const double *vel, double dt, void *stream) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (!isfinite(dt)) return fail(SPH_ERR_INVALID, "dt must be finite");
+    const long long n = g->n;
+    if (n > 0 && (!xyz_new || !vel)) return fail(SPH_ERR_INVALID, "xyz_new and vel are needed");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    if (g->p.precision != SPH_PREC_FP16_RCLL || n == 0) return sph_bin_cells(&g->p, xyz_new, n, stream, &grid);
+    SPH_TRY(ensure(g->rel64, (size_t)n * sizeof(double4), s));
+    SPH_TRY(ensure(g->rel64u, (size_t)n * sizeof(double4), s));
+    GridDev d = make_dev(g);
+    if (!g->rel64_valid || g->drift > DRIFT_BUDGET) {
+        // derive the FP64 relative coordinates from the current positions
+        SPH_CUDA(launch_rel64_sync(d, P<int>(g->scell), g->xyz, P<double4>(g->rel64), g->sm_count, s));
+        g->rel64_valid = true;
+        g->drift = 0;
+    }
+    SPH_CUDA(launch_status_init(P<DevStatus>(g->status), s));
+    SPH_CUDA(launch_advance(d, P<int>(g->scell), P<double4>(g->rel64), vel, dt, P<int>(g->cnt), P<int>(g->cid),
+                            P<int>(g->slot), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4>(g->rel64u),
+                            g->sm_count, s));
+    SPH_TRY(read_status(g));
+    if (g->h_status->flags & ST_NONFINITE) return fail(SPH_ERR_INVALID, "non-finite velocity or displacement");
+    if (g->h_status->flags & ST_OUT_OF_BOX) {
+        if (g->p.have_box) return fail(SPH_ERR_INVALID, "a particle left the given box");
+        // a particle left the grid: bin again with the new bounds
+        return sph_bin_cells(&g->p, xyz_new, n, stream, &grid);
+    }
+    // drift bound of this step: the FMA of Eq. 8, the rounding of v dt and of
+    // 2/h_c, and the caller's rounding of x + v dt, relative 2^-53 each
+    double dmax = 0;
+    {
+        const unsigned long long b = g->h_status->max_key[0];
+        memcpy(&dmax, &b, 8);
+    }
+    double xmax = 0;
+    for (int k = 0; k < g->p.dim; ++k) {
+        const double a = fabs(g->lo[k]), b = fabs(g->lo[k] + g->nk[k] * g->hc);
+        xmax = fmax(xmax, fmax(a, b));
+    }
+    const double du = dmax * d.two_over_hc, xu = xmax * d.two_over_hc;
+    g->drift += 0x1p-53 * (3.0 + 2.0 * du + 2.0 * (xu + du));
+    SPH_CUDA(launch_order_convert(d, (int)n, g->p.dim, SPH_PREC_FP16_RCLL, P<int>(g->cnt), P<int>(g->cid),
+                                  P<int>(g->slot), P<int>(g->cell_start), P<int>(g->orig_id), P<int>(g->rank),
+                                  P<int>(g->scell), P<uint2>(g->rel16), P<float4>(g->rel32), P<uint2>(g->rel16u),
+                                  P<float4>(g->rel32u), P<double4>(g->rel64u), P<double4>(g->rel64), nullptr,
+                                  g->scan_tmp.p, P<int>(g->big_list), &P<DevStatus>(g->status)->big_cells,
+                                  g->sm_count, s));
+    g->xyz = xyz_new;
+    return SPH_OK;
 }
 
 extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity,
@@ -499,7 +561,7 @@ extern "C" int sph_grid_free(sph_grid_t grid) {
     if (!g) return SPH_OK;
     cudaStream_t s = g->stream;
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
-                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->x64, &g->scan_tmp, &g->big_list,
+                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->rel64, &g->rel64u, &g->x64, &g->scan_tmp, &g->big_list,
                       &g->rowcnt, &g->tmp_rp, &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
                       &g->tstate, &g->scell_x, &g->tcount, &g->toff, &g->tiles};
     for (DevBuf *b : bufs) release(*b, s);

@@ -159,7 +159,8 @@ template <int PREC>
 __global__ void k_convert(int n, int dim, GridDev g, const int *__restrict__ cid_in,
                           int *__restrict__ rank, int *__restrict__ scell, uint2 *__restrict__ rel16,
                           float4 *__restrict__ rel32, const uint2 *__restrict__ rel16u,
-                          const float4 *__restrict__ rel32u, double4 *__restrict__ x64) {
+                          const float4 *__restrict__ rel32u, const double4 *__restrict__ rel64u,
+                          double4 *__restrict__ rel64, double4 *__restrict__ x64) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
         const int i = g.orig_id[s];
@@ -172,6 +173,7 @@ __global__ void k_convert(int n, int dim, GridDev g, const int *__restrict__ cid
         } else {
             rel16[s] = rel16u[i];
             rel32[s] = rel32u[i];
+            if (rel64 != nullptr) rel64[s] = rel64u[i];
         }
     }
 }
@@ -201,6 +203,33 @@ cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st
     return cudaGetLastError();
 }
 
+cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
+                                 int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
+                                 const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,
+                                 double4 *x64, void *scan_tmp, int *big_list, unsigned int *big_count, int sm_count,
+                                 cudaStream_t s) {
+    const int nt = 256;
+    const unsigned blocks = grid_for(n, nt, sm_count, 16);
+    cudaError_t e = exclusive_scan_i32(cnt, cell_start, g.ncell, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(TAG_SCATTER, s);
+        note_launch(1);
+        k_scatter<<<blocks, nt, 0, s>>>(n, cell_start, cid, slot, orig_id);
+    }
+    e = segmented_sort_i32(orig_id, cell_start, g.ncell, big_list, big_count, s);
+    if (e != cudaSuccess) return e;
+    ProfScope ps(TAG_CONVERT, s);
+    note_launch(1);
+    if (prec == SPH_PREC_FP16_RCLL)
+        k_convert<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, rel16, rel32, rel16u,
+                                                            rel32u, rel64u, rel64, nullptr);
+    else
+        k_convert<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, nullptr, nullptr, nullptr,
+                                                           nullptr, nullptr, nullptr, x64);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec,
                                         int *cnt, int *cid, int *slot, int *cell_start, int *orig_id,
                                         int *rank, int *scell, uint2 *rel16, float4 *rel32, uint2 *rel16u,
@@ -220,24 +249,12 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
             k_hash<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot, nullptr, nullptr,
                                                             check_box);
     }
-    e = exclusive_scan_i32(cnt, cell_start, g.ncell, scan_tmp, s);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    {
-        ProfScope ps(TAG_SCATTER, s);
-        note_launch(1);
-        k_scatter<<<blocks, nt, 0, s>>>(n, cell_start, cid, slot, orig_id);
-    }
-    e = segmented_sort_i32(orig_id, cell_start, g.ncell, big_list, big_count, s);
-    if (e != cudaSuccess) return e;
-    ProfScope ps(TAG_CONVERT, s);
-    note_launch(1);
-    if (prec == SPH_PREC_FP16_RCLL)
-        k_convert<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, rel16, rel32,
-                                                            rel16u, rel32u, nullptr);
-    else
-        k_convert<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, nullptr, nullptr,
-                                                           nullptr, nullptr, x64);
-    return cudaGetLastError();
+    // a fresh binning leaves the FP64 relative coordinates (kept for time
+    // steps) to be derived again on the next step
+    return launch_order_convert(g, n, dim, prec, cnt, cid, slot, cell_start, orig_id, rank, scell, rel16, rel32,
+                                rel16u, rel32u, nullptr, nullptr, x64, scan_tmp, big_list, big_count, sm_count, s);
 }
 
 }  // namespace sph

@@ -15,8 +15,29 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
                                         uint2 *rel16, float4 *rel32, uint2 *rel16u, float4 *rel32u, double4 *x64,
                                         void *scan_tmp, int *big_list, unsigned int *big_count, int check_box,
                                         int sm_count, cudaStream_t s);
+// Scan of the cell histogram, scatter, per-cell sort and the gather of the
+// input-order arrays (cid, rel16u, rel32u and, if not NULL, rel64u) into
+// cell order: the second half of binning, shared with the time step.
+cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
+                                 int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
+                                 const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,
+                                 double4 *x64, void *scan_tmp, int *big_list, unsigned int *big_count, int sm_count,
+                                 cudaStream_t s);
 cudaError_t launch_scatter(int n, const int *cell_start, const int *cid, const int *slot, int *orig_id,
                            int sm_count, cudaStream_t s);
+
+// Time step of Eq. 8-9 (advance.cu).  Relative coordinates of the sorted
+// particles (rel64) advanced by 2 v dt / h_c, cell shifts where they leave
+// [-1, 1]; input-order outputs (cid, slot with the histogram cnt, rel16u,
+// rel32u, rel64u) ready for launch_order_convert.  Status: ST_OUT_OF_BOX when
+// a particle leaves the grid, max |v dt| as a key in max_key[0].
+cudaError_t launch_advance(const GridDev &g, const int *scell, const double4 *rel64, const double *vel, double dt,
+                           int *cnt, int *cid, int *slot, uint2 *rel16u, float4 *rel32u, double4 *rel64u,
+                           int sm_count, cudaStream_t s);
+// FP64 relative coordinates of the sorted particles from positions xyz in
+// their current cells (the conversion of binning, cells unchanged).
+cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *xyz, double4 *rel64, int sm_count,
+                              cudaStream_t s);
 
 // Two-pass search, unfused density, canonical order (search.cu).
 cudaError_t launch_nnps(const GridDev &g, int prec, int mode_fill, int *cnt, const long long *row_ptr, int *col,

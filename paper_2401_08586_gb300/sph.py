@@ -135,6 +135,7 @@ def load(build_if_missing=False):
         "sph_launch_count": [],
         "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
         "sph_nnps_query_static": [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp],
+        "sph_advance": [_vp, _vp, _vp, ctypes.c_double, _vp],
         "sph_batch_run": [ctypes.POINTER(_vp), ctypes.POINTER(sph_params), ctypes.POINTER(_vp),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(sph_batch_out), _vp],
         "sph_batch_get_stats": [_vp, ctypes.POINTER(sph_batch_stats)],
@@ -166,7 +167,7 @@ def exported_symbols():
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
-            "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
+            "sph_advance", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
             "sph_server_create", "sph_serve_submit", "sph_serve_poll", "sph_serve_wait", "sph_result_copy",
             "sph_result_release", "sph_server_get_stats", "sph_server_destroy"]
 
@@ -326,6 +327,11 @@ def _host_ptr(a):
 
 
 # ---- convenience ------------------------------------------------------------
+
+def sph_advance(grid, xyz_new, vel, dt, stream=None):
+    """Eq. 8-9 time step of a binned grid (see include/sph.h)."""
+    _check(load().sph_advance(grid, _ptr(xyz_new), _ptr(vel), float(dt), _stream(stream)))
+
 
 def sph_batch_run(batch, params_list, xyz_list, out, stream=None):
     """One batched run.  batch: workspace handle (None on first use); params_list:
@@ -582,6 +588,13 @@ class Grid:
         self.params = make_params(self.xyz.shape[1], h, kh, order, precision, mass, cell_size, box)
         self.handle = None
         self.handle = sph_bin_cells(self.params, self.xyz, self.xyz.shape[0], stream, None)
+
+    def advance(self, xyz_new, vel, dt, stream=None):
+        """Eq. 8-9 step: positions after the step and the velocities (CUDA
+        float64 tensors, input order)."""
+        self.xyz = xyz_new.contiguous()
+        self._vel = vel.contiguous()
+        sph_advance(self.handle, self.xyz, self._vel, dt, stream)
 
     def rebin(self, xyz=None, stream=None):
         if xyz is not None:
