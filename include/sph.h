@@ -163,6 +163,20 @@ int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col,
                     void *stream);
 
 /*
+ * Volume-free normalised first-order gradient of a particle field f
+ * (Appendix Eq. A5): for each axis a,
+ *   grad_a f_i = sum_j (f_j - f_i) dW_ij/dx^a / sum_j (x_j^a - x_i^a) dW_ij/dx^a
+ * over the neighbour list of sph_nnps_query (same row order and column
+ * convention as the grid's order), W from Eq. 3.  f: device FP64[n] in input
+ * order; grad: device FP64[n * dim], rows in the CSR's row order.  Distances
+ * from the FP32 relative coordinates, f_j - f_i from a float hi/lo split of f,
+ * sums in FP32 (relative error ~1e-6 of the result's scale); an axis whose
+ * denominator is zero gives 0.  FP16-RCLL grids only.  Enqueued on `stream`.
+ */
+int sph_gradient_a5(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, const double *f, double *grad,
+                    void *stream);
+
+/*
  * The neighbour search of sph_nnps_query (cell order, FP16-RCLL, fused
  * density, single pass over row tiles) for callers that cannot allocate
  * device memory when they call it.  Typical such callers: a process whose

@@ -35,6 +35,7 @@ struct sph_grid_s {
     int staging = -1;       // extra staging bytes of the tile search (SPH_OPT_STAGING; -1: automatic)
     double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
     DevBuf rel64, rel64u;   // FP64 relative coordinates kept across time steps (cell / input order)
+    DevBuf fsplit;          // gradient: the field as float hi + lo in cell order
     bool rel64_valid = false;
     double drift = 0;       // bound on |rel64 - conversion of xyz| in units of u
     long long own_nnz = 0;
@@ -394,6 +395,23 @@ extern "C" int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const in
     return SPH_OK;
 }
 
+extern "C" int sph_gradient_a5(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, const double *f,
+                               double *grad, void *stream) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (!row_ptr || !f || !grad || (!col && g->n > 0)) return fail(SPH_ERR_INVALID, "NULL argument");
+    if (g->p.precision != SPH_PREC_FP16_RCLL) return fail(SPH_ERR_INVALID, "the gradient needs an FP16-RCLL grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    if (g->n == 0) return SPH_OK;
+    SPH_TRY(ensure(g->fsplit, (size_t)g->n * sizeof(float2), s));
+    GridDev d = make_dev(g);
+    SPH_CUDA(launch_gradient_a5(d, P<int>(g->rank), P<int>(g->scell), reinterpret_cast<const long long *>(row_ptr),
+                                col, g->p.order == SPH_ORDER_CANONICAL, f, P<float2>(g->fsplit), grad, g->sm_count,
+                                s));
+    return SPH_OK;
+}
+
 extern "C" int sph_grid_info_get(sph_grid_t grid, sph_grid_info *info) {
     sph_grid_s *g = grid;
     if (!g || !info) return fail(SPH_ERR_INVALID, "NULL argument");
@@ -561,7 +579,7 @@ extern "C" int sph_grid_free(sph_grid_t grid) {
     if (!g) return SPH_OK;
     cudaStream_t s = g->stream;
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
-                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->rel64, &g->rel64u, &g->x64, &g->scan_tmp, &g->big_list,
+                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->rel64, &g->rel64u, &g->fsplit, &g->x64, &g->scan_tmp, &g->big_list,
                       &g->rowcnt, &g->tmp_rp, &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
                       &g->tstate, &g->scell_x, &g->tcount, &g->toff, &g->tiles};
     for (DevBuf *b : bufs) release(*b, s);

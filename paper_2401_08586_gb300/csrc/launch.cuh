@@ -48,6 +48,11 @@ cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long 
                          const float *rho_cell, int *cnt_tmp, void *scan_tmp, long long *rp, int *col, float *rho,
                          int *big_list, unsigned int *big_count, int sm_count, cudaStream_t s);
 
+// Appendix Eq. A5 gradient over a CSR (gradient.cu); fs: float2 scratch of n.
+cudaError_t launch_gradient_a5(const GridDev &g, const int *rank, const int *scell, const long long *row_ptr,
+                               const int *col, int canonical, const double *f, float2 *fs, double *grad,
+                               int sm_count, cudaStream_t s);
+
 // Single-pass search, one CTA per cell (nnps_fused.cu).
 cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, long long cap, float *rho,
                               unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);

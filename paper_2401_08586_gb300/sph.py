@@ -136,6 +136,7 @@ def load(build_if_missing=False):
         "sph_grid_set_option": [_vp, ctypes.c_int, ctypes.c_int64],
         "sph_nnps_query_static": [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp],
         "sph_advance": [_vp, _vp, _vp, ctypes.c_double, _vp],
+        "sph_gradient_a5": [_vp, _vp, _vp, _vp, _vp, _vp],
         "sph_batch_run": [ctypes.POINTER(_vp), ctypes.POINTER(sph_params), ctypes.POINTER(_vp),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(sph_batch_out), _vp],
         "sph_batch_get_stats": [_vp, ctypes.POINTER(sph_batch_stats)],
@@ -167,7 +168,7 @@ def exported_symbols():
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
-            "sph_advance", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
+            "sph_advance", "sph_gradient_a5", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
             "sph_server_create", "sph_serve_submit", "sph_serve_poll", "sph_serve_wait", "sph_result_copy",
             "sph_result_release", "sph_server_get_stats", "sph_server_destroy"]
 
@@ -327,6 +328,11 @@ def _host_ptr(a):
 
 
 # ---- convenience ------------------------------------------------------------
+
+def sph_gradient_a5(grid, row_ptr, col, f, grad, stream=None):
+    """Appendix Eq. A5 gradient of f over the grid's CSR into grad (n x dim)."""
+    _check(load().sph_gradient_a5(grid, _ptr(row_ptr), _ptr(col), _ptr(f), _ptr(grad), _stream(stream)))
+
 
 def sph_advance(grid, xyz_new, vel, dt, stream=None):
     """Eq. 8-9 time step of a binned grid (see include/sph.h)."""
@@ -588,6 +594,14 @@ class Grid:
         self.params = make_params(self.xyz.shape[1], h, kh, order, precision, mass, cell_size, box)
         self.handle = None
         self.handle = sph_bin_cells(self.params, self.xyz, self.xyz.shape[0], stream, None)
+
+    def gradient(self, row_ptr, col, f, stream=None):
+        """Appendix Eq. A5 gradient (n x dim float64 CUDA tensor) of the field
+        f (float64, input order) over the CSR of :meth:`query`."""
+        import torch
+        g = torch.empty((self.n, self.xyz.shape[1]), dtype=torch.float64, device=self.xyz.device)
+        sph_gradient_a5(self.handle, row_ptr, col, f.contiguous(), g, stream)
+        return g
 
     def advance(self, xyz_new, vel, dt, stream=None):
         """Eq. 8-9 step: positions after the step and the velocities (CUDA
