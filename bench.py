@@ -402,6 +402,8 @@ def main():
             line["e2e"]["value"] = world * n * args.steps / replicas.max_over_ranks(line["e2e"]["seconds"], world,
                                                                                     dev)
         line["e2e"].pop("seconds", None)
+        line["gradient_a5"] = bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, args.steps)
+        line["timestep"] = bench_timestep(sph, ps, xyz, dev, stream, row_ptr, col, cap, rho, args.steps)
         line["serving"] = bench_serve(sph, dev, count=450, warm=50)
         if world == 1 and rank == 0:
             line["cpu_baseline"] = cpu_baseline(ps)
@@ -445,6 +447,75 @@ def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value):
     v = n * steps / (sum(ms) / 1e3)
     return {"value": v, "unit": "particles/s", "ms_per_step": sum(ms) / steps, "steps": steps,
             "fp16_rcll_speedup": fp16_value / v}
+
+
+def bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, steps):
+    """The Appendix Eq. A5 gradient of f = x^3 over the step's CSR (the
+    paper's second timed kernel), CUDA events on the stream."""
+    import torch
+    f = (xyz[:, 0] ** 3).contiguous()
+    # the grid's last query wrote row_ptr / col in cell order
+    out = torch.empty((ps.n, ps.dim), dtype=torch.float64, device=dev)
+    sptr = stream.cuda_stream
+    ms = []
+    for k in range(steps + 3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sph.sph_gradient_a5(grid, row_ptr, col, f, out, sptr)
+        b.record(stream)
+        b.synchronize()
+        if k >= 3:
+            ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    return {"ms": t, "particles_per_s": ps.n / (t * 1e-3), "field": "x^3"}
+
+
+def bench_timestep(sph, ps, xyz, dev, stream, row_ptr, col, cap, rho, steps):
+    """One SPH time step's search through the Eq. 8-9 update (sph_advance +
+    query) against re-binning the moved positions (sph_bin_cells + query).
+    The particles move back and forth by a random displacement of up to
+    0.15 dx per axis, so about a fifth of them change cell every step."""
+    import torch
+    sptr = stream.cuda_stream
+    n = ps.n
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    v = (torch.rand(xyz.shape, generator=g, device=dev, dtype=torch.float64) * 2 - 1) * (0.15 * ps.dx)
+    xs = [xyz, xyz + v]
+    vs = [-v, v]
+    params = sph.make_params(ps.dim, ps.h, ps.kh, order=sph.SPH_ORDER_CELL)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        ms = []
+        for k in range(steps + 3):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(k)
+            b.record(stream)
+            b.synchronize()
+            if k >= 3:
+                ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    grid = sph.sph_bin_cells(params, xs[0], n, sptr, None)
+
+    def adv(k):
+        sph.sph_advance(grid, xs[(k + 1) % 2], vs[(k + 1) % 2], 1.0, sptr)
+        sph.sph_nnps_query(grid, row_ptr, col, cap, False, rho, sptr)
+
+    def rebin(k):
+        sph.sph_bin_cells(params, xs[(k + 1) % 2], n, sptr, grid)
+        sph.sph_nnps_query(grid, row_ptr, col, cap, False, rho, sptr)
+
+    ms_adv = timed(adv)
+    sph.sph_bin_cells(params, xs[0], n, sptr, grid)
+    ms_bin = timed(rebin)
+    sph.sph_grid_check(grid, sptr)
+    sph.sph_grid_free(grid)
+    return {"advance_plus_query_ms": ms_adv, "rebin_plus_query_ms": ms_bin,
+            "advance_particles_per_s": n / (ms_adv * 1e-3), "displacement": "U(+-0.15 dx) per axis, back and forth"}
 
 
 def bench_e2e(sph, ps, dev, stream, args):

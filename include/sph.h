@@ -177,6 +177,26 @@ int sph_gradient_a5(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col,
                     void *stream);
 
 /*
+ * Precision study of the neighbour decision (Tables 1-2, approach II of
+ * Table 4): over every candidate pair (i, j != i) of the cell link-list with
+ * i's input index in [row_begin, row_end), count the decisions that differ
+ * from the FP64 definition when made with FP16 or FP32 absolute coordinates,
+ * with FP16 cell-relative coordinates alone (the paper's FP16 RCLL), and with
+ * this library's tiered decision (0 by construction).  An instrument, not a
+ * search: one thread per particle.  FP16-RCLL grids.  Synchronises `stream`.
+ */
+typedef struct {
+    int64_t candidates;       /* ordered pairs tested */
+    int64_t neighbours;       /* pairs with r^2 < kh^2 in FP64 */
+    int64_t wrong_fp16_abs;   /* FP16 absolute coordinates: decisions != FP64 */
+    int64_t wrong_fp32_abs;   /* FP32 absolute coordinates */
+    int64_t wrong_fp16_rcll;  /* FP16 relative coordinates, FP16 decision alone */
+    int64_t wrong_tiered;     /* FP16 band, FP32 band, FP64 tier */
+} sph_precision_counts;
+int sph_precision_study(sph_grid_t grid, int64_t row_begin, int64_t row_end, sph_precision_counts *out,
+                        void *stream);
+
+/*
  * The neighbour search of sph_nnps_query (cell order, FP16-RCLL, fused
  * density, single pass over row tiles) for callers that cannot allocate
  * device memory when they call it.  Typical such callers: a process whose

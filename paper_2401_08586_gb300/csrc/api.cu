@@ -36,6 +36,7 @@ struct sph_grid_s {
     double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
     DevBuf rel64, rel64u;   // FP64 relative coordinates kept across time steps (cell / input order)
     DevBuf fsplit;          // gradient: the field as float hi + lo in cell order
+    DevBuf study;           // precision study counters
     bool rel64_valid = false;
     double drift = 0;       // bound on |rel64 - conversion of xyz| in units of u
     long long own_nnz = 0;
@@ -412,6 +413,31 @@ extern "C" int sph_gradient_a5(sph_grid_t grid, const int64_t *row_ptr, const in
     return SPH_OK;
 }
 
+extern "C" int sph_precision_study(sph_grid_t grid, int64_t row_begin, int64_t row_end, sph_precision_counts *out,
+                                   void *stream) {
+    sph_grid_s *g = grid;
+    if (!g || !out) return fail(SPH_ERR_INVALID, "NULL argument");
+    if (g->p.precision != SPH_PREC_FP16_RCLL) return fail(SPH_ERR_INVALID, "the study needs an FP16-RCLL grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    memset(out, 0, sizeof(*out));
+    if (g->n == 0) return SPH_OK;
+    SPH_TRY(ensure(g->study, 6 * sizeof(unsigned long long), s));
+    GridDev d = make_dev(g);
+    SPH_CUDA(launch_precision_study(d, P<int>(g->scell), row_begin, row_end, g->p.kh, P<unsigned long long>(g->study),
+                                    g->sm_count, s));
+    unsigned long long h[6];
+    SPH_CUDA(cudaMemcpyAsync(h, g->study.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    out->candidates = (int64_t)h[0];
+    out->neighbours = (int64_t)h[1];
+    out->wrong_fp16_abs = (int64_t)h[2];
+    out->wrong_fp32_abs = (int64_t)h[3];
+    out->wrong_fp16_rcll = (int64_t)h[4];
+    out->wrong_tiered = (int64_t)h[5];
+    return SPH_OK;
+}
+
 extern "C" int sph_grid_info_get(sph_grid_t grid, sph_grid_info *info) {
     sph_grid_s *g = grid;
     if (!g || !info) return fail(SPH_ERR_INVALID, "NULL argument");
@@ -579,7 +605,7 @@ extern "C" int sph_grid_free(sph_grid_t grid) {
     if (!g) return SPH_OK;
     cudaStream_t s = g->stream;
     DevBuf *bufs[] = {&g->cell_start, &g->cnt, &g->cid, &g->slot, &g->orig_id, &g->rank, &g->scell,
-                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->rel64, &g->rel64u, &g->fsplit, &g->x64, &g->scan_tmp, &g->big_list,
+                      &g->rel16, &g->rel32, &g->rel16u, &g->rel32u, &g->rel64, &g->rel64u, &g->fsplit, &g->study, &g->x64, &g->scan_tmp, &g->big_list,
                       &g->rowcnt, &g->tmp_rp, &g->tmp_col, &g->tmp_rho, &g->status, &g->own_xyz, &g->own_rp, &g->own_col, &g->own_rho,
                       &g->tstate, &g->scell_x, &g->tcount, &g->toff, &g->tiles};
     for (DevBuf *b : bufs) release(*b, s);

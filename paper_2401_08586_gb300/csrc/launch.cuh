@@ -53,6 +53,13 @@ cudaError_t launch_gradient_a5(const GridDev &g, const int *rank, const int *sce
                                const int *col, int canonical, const double *f, float2 *fs, double *grad,
                                int sm_count, cudaStream_t s);
 
+// Precision study of the neighbour decision (study.cu): out[0..5] =
+// candidates, neighbours, wrong FP16 absolute, wrong FP32 absolute, wrong
+// FP16 RCLL alone, wrong tiered; rows restricted to input indices
+// [row_begin, row_end).
+cudaError_t launch_precision_study(const GridDev &g, const int *scell, long long row_begin, long long row_end,
+                                   double kh, unsigned long long *out, int sm_count, cudaStream_t s);
+
 // Single-pass search, one CTA per cell (nnps_fused.cu).
 cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, long long cap, float *rho,
                               unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);

@@ -90,6 +90,12 @@ class sph_server_stats(ctypes.Structure):
                 ("peak_held_bytes", ctypes.c_int64), ("queued", ctypes.c_int64)]
 
 
+class sph_precision_counts(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64), ("neighbours", ctypes.c_int64), ("wrong_fp16_abs", ctypes.c_int64),
+                ("wrong_fp32_abs", ctypes.c_int64), ("wrong_fp16_rcll", ctypes.c_int64),
+                ("wrong_tiered", ctypes.c_int64)]
+
+
 SPH_BATCH_OPT_GRAPH = 1
 SPH_BATCH_OPT_STAGING = 2
 
@@ -137,6 +143,7 @@ def load(build_if_missing=False):
         "sph_nnps_query_static": [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp],
         "sph_advance": [_vp, _vp, _vp, ctypes.c_double, _vp],
         "sph_gradient_a5": [_vp, _vp, _vp, _vp, _vp, _vp],
+        "sph_precision_study": [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(sph_precision_counts), _vp],
         "sph_batch_run": [ctypes.POINTER(_vp), ctypes.POINTER(sph_params), ctypes.POINTER(_vp),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(sph_batch_out), _vp],
         "sph_batch_get_stats": [_vp, ctypes.POINTER(sph_batch_stats)],
@@ -168,7 +175,7 @@ def exported_symbols():
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
-            "sph_advance", "sph_gradient_a5", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
+            "sph_advance", "sph_gradient_a5", "sph_precision_study", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
             "sph_server_create", "sph_serve_submit", "sph_serve_poll", "sph_serve_wait", "sph_result_copy",
             "sph_result_release", "sph_server_get_stats", "sph_server_destroy"]
 
@@ -332,6 +339,15 @@ def _host_ptr(a):
 def sph_gradient_a5(grid, row_ptr, col, f, grad, stream=None):
     """Appendix Eq. A5 gradient of f over the grid's CSR into grad (n x dim)."""
     _check(load().sph_gradient_a5(grid, _ptr(row_ptr), _ptr(col), _ptr(f), _ptr(grad), _stream(stream)))
+
+
+def sph_precision_study(grid, row_begin=0, row_end=None, stream=None):
+    """Wrong-decision counts of reduced-precision neighbour tests (dict)."""
+    c = sph_precision_counts()
+    if row_end is None:
+        row_end = 1 << 62
+    _check(load().sph_precision_study(grid, int(row_begin), int(row_end), ctypes.byref(c), _stream(stream)))
+    return {k: getattr(c, k) for k, _ in sph_precision_counts._fields_}
 
 
 def sph_advance(grid, xyz_new, vel, dt, stream=None):
