@@ -249,6 +249,11 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *     A tile whose output does not fit writes its rows directly (same
  *     result); more staging lowers the number of resident warps. */
 #define SPH_OPT_STAGING 2
+/*   SPH_OPT_TILE_SHAPE: shared-memory shape of the tile search: -1 (default)
+ *     chosen from the neighbours per particle, 0 sparse (up to 768 kept
+ *     candidates per pass of a tile, 16 resident warps per SM), 1 dense (1024,
+ *     13 warps).  Same results either way. */
+#define SPH_OPT_TILE_SHAPE 3
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 
 /* Fill *info (host) with the grid's sizes and device pointers.  The pointers
@@ -363,6 +368,8 @@ typedef struct {
     int64_t graph_replays;    /* runs that replayed the recorded graph */
     int32_t tuned_staging;    /* staging bytes chosen by the last tuning, -1: none yet */
     int32_t tuned_candidates; /* candidates timed by the last tuning */
+    int32_t tuned_shape;      /* tile shape chosen by the last tuning (SPH_OPT_TILE_SHAPE values), -1: none */
+    int32_t reserved;
     int64_t fp32_pairs;       /* last run: pairs re-decided in FP32 */
     int64_t fp64_pairs;       /* last run: pairs decided in FP64 */
 } sph_batch_stats;
@@ -372,11 +379,12 @@ int sph_batch_get_stats(sph_batch_t batch, sph_batch_stats *stats);
  *   (after the bounds, before the search) as a CUDA graph and replay it while
  *   the batch's sizes and buffers are unchanged; 0 launch directly every time.
  *   The search is one direct launch either way.
- * SPH_BATCH_OPT_STAGING: -1 (default) tune the tile search's staging bytes by
- *   timing 0, 2048, 4096 and 8192 on the first run of each density class
- *   (dimension and neighbours per particle to a quarter octave) and reuse the
- *   winner; -2 size it from the particle density without timing; 0 .. 65536
- *   in multiples of 16 fix it. */
+ * SPH_BATCH_OPT_STAGING: -1 (default) tune the tile search's shape and
+ *   staging bytes by timing five candidates (sparse 0 / 2048, dense 0 / 2048 /
+ *   4096) on the first run of each density class (dimension and neighbours per
+ *   particle to a quarter octave) and reuse the winner; -2 choose both from
+ *   the particle density without timing; 0 .. 65536 in multiples of 16 fix the
+ *   staging (shape from the density). */
 #define SPH_BATCH_OPT_GRAPH 1
 #define SPH_BATCH_OPT_STAGING 2
 int sph_batch_set_option(sph_batch_t batch, int option, int64_t value);

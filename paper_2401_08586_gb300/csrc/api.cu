@@ -33,6 +33,7 @@ struct sph_grid_s {
         toff, tiles;
     int fused_enabled = 1;  // search variant for cell-order FP16 queries (SPH_OPT_FUSED)
     int staging = -1;       // extra staging bytes of the tile search (SPH_OPT_STAGING; -1: automatic)
+    int tile_shape = -1;    // shared-memory shape of the tile search (SPH_OPT_TILE_SHAPE; -1: automatic)
     double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
     DevBuf rel64, rel64u;   // FP64 relative coordinates kept across time steps (cell / input order)
     DevBuf fsplit;          // gradient: the field as float hi + lo in cell order
@@ -312,20 +313,18 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         d = make_dev(g);
         SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), P<int>(g->tcount), P<long long>(g->toff),
                               g->scan_tmp.p, P<int4>(g->tiles), g->sm_count, s));
-        int extra = g->staging;
-        if (extra < 0) {
-            // neighbours per particle: the last measured value, else the
-            // uniform-density estimate (particles per cell x the search
-            // sphere's volume in cells)
-            double nbr = g->last_nbr;
-            if (nbr <= 0) {
-                const double ppc = (double)n / (double)g->ncell, r = g->p.kh / g->hc;
-                nbr = g->p.dim == 3 ? ppc * 4.18879 * r * r * r : ppc * 3.14159 * r * r;
-            }
-            extra = tile_extra_smem(nbr);
+        // neighbours per particle: the last measured value, else the
+        // uniform-density estimate (particles per cell x the search sphere's
+        // volume in cells)
+        double nbr = g->last_nbr;
+        if (nbr <= 0) {
+            const double ppc = (double)n / (double)g->ncell, r = g->p.kh / g->hc;
+            nbr = g->p.dim == 3 ? ppc * 4.18879 * r * r * r : ppc * 3.14159 * r * r;
         }
+        TileLaunch tv = tile_choose(nbr, g->tile_shape);
+        if (g->staging >= 0) tv.extra = g->staging;
         SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell,
-                                  col, col_capacity, rho, P<unsigned long long>(g->tstate), extra, g->sm_count, s));
+                                  col, col_capacity, rho, P<unsigned long long>(g->tstate), tv, g->sm_count, s));
     } else {
         SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
         SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
@@ -481,6 +480,11 @@ extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
     if (option == SPH_OPT_FUSED) {
         if (value < 0 || value > 2) return fail(SPH_ERR_INVALID, "SPH_OPT_FUSED takes 0, 1 or 2");
         g->fused_enabled = (int)value;
+        return SPH_OK;
+    }
+    if (option == SPH_OPT_TILE_SHAPE) {
+        if (value < -1 || value > 1) return fail(SPH_ERR_INVALID, "SPH_OPT_TILE_SHAPE takes -1, 0 or 1");
+        g->tile_shape = (int)value;
         return SPH_OK;
     }
     if (option == SPH_OPT_STAGING) {

@@ -224,7 +224,7 @@ struct sph_batch_s {
     long long graph_launches = 0;  // kernels per replay
     bool use_graph = true;
     int staging = -1;  // -1: autotune, -2: size from the density estimate without timing
-    std::map<int, int> tuned;  // density class -> staging bytes
+    std::map<int, TileLaunch> tuned;  // density class -> tile shape and staging bytes
     sph_batch_stats stats;
 };
 
@@ -263,6 +263,7 @@ static int batch_create(sph_batch_s **out) {
     memset(&b->key, 0, sizeof(b->key));
     memset(&b->stats, 0, sizeof(b->stats));
     b->stats.tuned_staging = -1;
+    b->stats.tuned_shape = -1;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_status, sizeof(DevStatus));
@@ -329,7 +330,7 @@ static cudaError_t batch_prep(sph_batch_s *b, int nsys, int dim, long long ntot,
 
 // The tile search over all systems' tiles (one persistent launch).
 static cudaError_t batch_search(sph_batch_s *b, int dim, long long ntot, long long nrow, long long ntiles_max,
-                                const sph_batch_out *out, int extra, cudaStream_t s) {
+                                const sph_batch_out *out, TileLaunch tv, cudaStream_t s) {
     GridDev g0;
     memset(&g0, 0, sizeof(g0));
     g0.dim = dim;
@@ -337,19 +338,19 @@ static cudaError_t batch_search(sph_batch_s *b, int dim, long long ntot, long lo
     g0.status = P<DevStatus>(b->status);
     return launch_nnps_tile(g0, P<GridDev>(b->gsys), P<int4>(b->tiles), P<long long>(b->toff) + nrow, ntiles_max,
                             reinterpret_cast<long long *>(out->row_ptr), out->col, out->col ? out->col_capacity : 0,
-                            out->rho, P<unsigned long long>(b->tstate), extra, b->sm_count, s);
+                            out->rho, P<unsigned long long>(b->tstate), tv, b->sm_count, s);
 }
 
 // Time one launch of the tile search (after a full sequence has prepared its
-// inputs) with `extra` staging bytes.
+// inputs) with shape and staging tv.
 static float time_search(sph_batch_s *b, int dim, long long ntot, long long nrow, long long ntiles_max,
-                         const sph_batch_out *out, int extra, cudaStream_t s) {
+                         const sph_batch_out *out, TileLaunch tv, cudaStream_t s) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     launch_status_reset_counters(P<DevStatus>(b->status), s);
     cudaEventRecord(e0, s);
-    cudaError_t err = batch_search(b, dim, ntot, nrow, ntiles_max, out, extra, s);
+    cudaError_t err = batch_search(b, dim, ntot, nrow, ntiles_max, out, tv, s);
     cudaEventRecord(e1, s);
     float ms = INFINITY;
     if (err == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
@@ -515,17 +516,14 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     // ---- staging size: fixed, tuned earlier for this density class, or tuned now
     const double nbr = ntot > 0 ? nbr_w / (double)ntot : 0.0;
     const int dclass = dim * 1000 + (nbr > 0 ? (int)floor(4.0 * log2(nbr)) : -999);
-    int extra = b->staging;
+    TileLaunch tv = tile_choose(nbr, -1);
     bool tune = false;
-    if (extra == -2) {
-        extra = tile_extra_smem(nbr);
-    } else if (extra < 0) {
+    if (b->staging >= 0) {
+        tv.extra = b->staging;
+    } else if (b->staging == -1) {
         auto it = b->tuned.find(dclass);
-        if (it != b->tuned.end()) extra = it->second;
-        else {
-            tune = ntot > 0 && out->col != nullptr;
-            extra = tile_extra_smem(nbr);
-        }
+        if (it != b->tuned.end()) tv = it->second;
+        else tune = ntot > 0 && out->col != nullptr;
     }
 
     // ---- the launch sequence: replayed graph, recorded graph or direct -----------
@@ -595,10 +593,11 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
         // the search: tuned candidates are timed here (each run leaves the
         // same result), then one launch with the chosen staging
         if (tune) {
-            const int cand[] = {0, 2048, 4096, 8192};
+            const TileLaunch cand[] = {{TILE_SPARSE, 0}, {TILE_SPARSE, 2048}, {TILE_DENSE, 0}, {TILE_DENSE, 2048},
+                                       {TILE_DENSE, 4096}};
             float best_ms = INFINITY;
-            int best = extra;
-            for (int c : cand) {
+            TileLaunch best = tv;
+            for (const TileLaunch &c : cand) {
                 const float ms = time_search(b, dim, ntot, nrow, ntiles_max, out, c, s);
                 if (ms < best_ms) {
                     best_ms = ms;
@@ -606,12 +605,13 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
                 }
             }
             b->tuned[dclass] = best;
-            b->stats.tuned_staging = best;
+            b->stats.tuned_staging = best.extra;
+            b->stats.tuned_shape = best.shape;
             b->stats.tuned_candidates = (int)(sizeof(cand) / sizeof(cand[0]));
-            extra = best;
+            tv = best;
         }
         SPH_CUDA(launch_status_reset_counters(P<DevStatus>(b->status), s));
-        SPH_CUDA(batch_search(b, dim, ntot, nrow, ntiles_max, out, extra, s));
+        SPH_CUDA(batch_search(b, dim, ntot, nrow, ntiles_max, out, tv, s));
     }
 
     // ---- nnz, status ------------------------------------------------------------

@@ -67,9 +67,18 @@ cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, lo
 // Single-pass search, one warp per row tile (nnps_tile.cu).
 cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
                          void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
+// Shared-memory shape of a tile-search launch: TILE_SPARSE (768 kept
+// candidates per pass, 16 warps per SM) or TILE_DENSE (1024, 13 per SM), and
+// extra dynamic shared memory for output staging.
+enum { TILE_SPARSE = 0, TILE_DENSE = 1 };
+struct TileLaunch {
+    int shape;
+    int extra;
+};
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
-                             unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s);
-int tile_extra_smem(double neighbours_per_particle);
+                             unsigned long long *tstate, TileLaunch v, int sm_count, cudaStream_t s);
+// Shape (shape < 0: chosen from nbr) and staging for about nbr neighbours per particle.
+TileLaunch tile_choose(double neighbours_per_particle, int shape);
 
 }  // namespace sph

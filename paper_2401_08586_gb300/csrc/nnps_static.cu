@@ -106,7 +106,7 @@ extern "C" int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t 
     cudaError_t e = launch_tiles(d, v.scell, scell_x, tcount, toff, scan_tmp, tiles, v.sm_count, s);
     if (e == cudaSuccess)
         e = launch_nnps_tile(d, nullptr, tiles, toff + v.nrow, ntiles_max, reinterpret_cast<long long *>(row_ptr), col,
-                             col_capacity, rho, tstate, 0, v.sm_count, s);
+                             col_capacity, rho, tstate, tile_choose(0.0, TILE_SPARSE), v.sm_count, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(SPH_ERR_CUDA, cudaGetErrorString(e));

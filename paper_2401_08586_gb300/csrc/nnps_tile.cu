@@ -29,8 +29,11 @@
 // and density, and emits its row from the kept bits.  Tiles with several
 // home groups or more than CMAX kept candidates run the steps twice (count,
 // then emit straight to their rows after the look-back).
+#include <stddef.h>
+
 #include <mutex>
 
+#include "launch.cuh"
 #include "nnps_common.cuh"
 
 namespace sph {
@@ -41,29 +44,41 @@ namespace {
 
 constexpr int TW = 32;        // rows per tile
 constexpr int SPANMAX = 4;    // home cells per group along x (keeps |X| < 8)
-constexpr int WIN = 256;      // kept candidates per staging window
-constexpr int CMAX = 1024;    // kept candidates per pass (bitmask length)
-constexpr int NWORD = CMAX / 32;
 constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the culling test
 constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch may ask for
-constexpr int STG_BASE_SLOTS = (WIN / 2 * 16 + WIN * 16) / 2;  // 16-bit output slots in pw + f32
+
+// Shared-memory shape of the tile search: kept candidates per pass (the
+// bitmask length) and per staging window.  The sparse shape needs 12.6 KB per
+// warp, so 16 one-warp CTAs fit an SM (the register limit); the dense shape
+// (15.6 KB, 13 per SM) keeps more candidates per pass for denser particle sets.
+template <int CMAX_, int WIN_>
+struct TileCfg {
+    static constexpr int CMAX = CMAX_;
+    static constexpr int WIN = WIN_;
+    static constexpr int NWORD = CMAX_ / 32;
+    static_assert(CMAX_ % 32 == 0 && WIN_ % 32 == 0 && WIN_ <= CMAX_, "tile shape");
+};
+using TileSparse = TileCfg<768, 224>;
+using TileDense = TileCfg<1024, 256>;
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
 constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 constexpr int LOOKBACK_SPIN_LIMIT = 1 << 20;
 
+template <class C>
 struct TileSmem {
-    unsigned int S[TW][NWORD + 1];
-    int jall[CMAX];            // kept candidates: sorted index
-    unsigned char code[CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5
-    int selfpos[TW];           // kept slot of each lane's own particle (-1: not in this fill)
-    int rstart[9], rlen[9], rb[9][8];
-    // pw and f32 come last and are contiguous with any extra dynamic shared
-    // memory of the launch: after the last window they hold the tile's staged
-    // output (16-bit kept-candidate slots), stg_slots of them
-    uint4 pw[WIN / 2];  // FP16 pairs: word (g*16 + b) = kept candidates 32g + b (lo), 32g + 16 + b (hi)
-    float4 f32[WIN];    // FP32 frame coordinates, candidate index j in .w
+    unsigned int S[TW][C::NWORD + 1];
+    int jall[C::CMAX];  // kept candidates: sorted index
+    int selfpos[TW];    // kept slot of each lane's own particle (-1: not in this fill)
+    int rstart[9], rlen[9], rcum[10], rb[9][8];  // candidate rows: start, length, flat prefix, cell bounds
+    // code, pw and f32 come last and are contiguous with any extra dynamic
+    // shared memory of the launch: after the last window they hold the tile's
+    // staged output (16-bit kept-candidate slots), stg_slots of them
+    unsigned char code[C::CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5
+    uint4 pw[C::WIN / 2];         // FP16 pairs: word (g*16 + b) = kept candidates 32g + b (lo), 32g + 16 + b (hi)
+    float4 f32[C::WIN];           // FP32 frame coordinates, candidate index j in .w
+    static constexpr size_t staging_bytes() { return sizeof(code) + sizeof(pw) + sizeof(f32); }
 };
 
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
@@ -161,8 +176,8 @@ struct Group {
 };
 
 // Candidate row table of a group (cells [xa, xb] of row (cy, cz)).
-template <int DIM>
-__device__ __forceinline__ void group_rows(TileSmem &S, const GridDev &g, int cy, int cz, const Group &G) {
+template <int DIM, class C>
+__device__ __forceinline__ void group_rows(TileSmem<C> &S, const GridDev &g, int cy, int cz, const Group &G) {
     constexpr int NROWS = DIM == 3 ? 9 : 3;
     const int lane = threadIdx.x & 31;
     const int nx = g.nk[0], ny = g.nk[1], nz = g.nk[2];
@@ -178,61 +193,79 @@ __device__ __forceinline__ void group_rows(TileSmem &S, const GridDev &g, int cy
         S.rb[r][k] = v;
     }
     __syncwarp();
+    int len = 0;
     if (lane < 9) {
         const int r = lane;
         const int a = S.rb[r][0];
         S.rstart[r] = a >= 0 ? a : 0;
-        S.rlen[r] = a >= 0 ? S.rb[r][G.nb - 1] - a : 0;
+        len = a >= 0 ? S.rb[r][G.nb - 1] - a : 0;
+        S.rlen[r] = len;
     }
+    // flat index of the candidates: rcum[r] = candidates in rows before r
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane < 9) S.rcum[lane + 1] = inc;
+    if (lane == 0) S.rcum[0] = 0;
     __syncwarp();
 }
 
-// Cull and compact candidates of the group, resuming at (cur_r, cur_base),
-// until the union is exhausted or the kept list cannot take another 32.
-// Returns the number kept; advances the cursor.
-template <int DIM>
-__device__ __forceinline__ int cull_fill(TileSmem &S, const GridDev &g, const Group &G, float cullT, int &cur_r,
-                                         int &cur_base, int p0, int nhome) {
+constexpr int CULL_CHUNKS = 4;  // chunks of 32 candidates whose loads are in flight together
+
+// Cull and compact candidates of the group, resuming at the flat candidate
+// index cur (rows in order, each row's candidates in order: ascending sorted
+// index), until the union is exhausted or the kept list cannot take another
+// 32.  Returns the number kept; advances the cursor.
+template <int DIM, class C>
+__device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const Group &G, float cullT, int &cur,
+                                         int p0, int nhome) {
     constexpr int NROWS = DIM == 3 ? 9 : 3;
+    constexpr int U = CULL_CHUNKS;
     const int lane = threadIdx.x & 31;
     S.selfpos[lane] = -1;
     __syncwarp();
-    int kept = 0;
-    while (cur_r < NROWS) {
-        const int len = S.rlen[cur_r];
-        if (cur_base >= len) {
-            ++cur_r;
-            cur_base = 0;
-            continue;
-        }
-        if (kept + 64 > CMAX) break;
-        const int r = cur_r;
-        const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
-        const int dz = DIM == 3 ? (r / 3) - 1 : 0;
-        // two chunks of 32 per step so that both loads are in flight together
-        int jk[2], ox[2];
-        bool valid[2];
-        uint2 q[2];
+    int rc[NROWS + 1];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int k = cur_base + 32 * u + lane;
-            valid[u] = k < len;
-            jk[u] = S.rstart[r] + k;
+    for (int r = 0; r <= NROWS; ++r) rc[r] = S.rcum[r];
+    const int total = rc[NROWS];
+    int kept = 0;
+    while (cur < total && kept + 32 <= C::CMAX) {
+        const int nu = kept + 32 * U <= C::CMAX ? U : 1;  // warp-uniform
+        int jk[U], rr[U];
+        bool valid[U];
+        uint2 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = cur + 32 * u + lane;
+            valid[u] = u < nu && k < total;
+            int r = 0, base = 0;  // row of flat index k and the row's first flat index
+#pragma unroll
+            for (int t = 1; t < NROWS; ++t) {
+                const bool past = k >= rc[t];
+                r += past ? 1 : 0;
+                base = past ? rc[t] : base;
+            }
+            rr[u] = r;
+            jk[u] = S.rstart[r] + (k - base);
             q[u] = valid[u] ? g.rel16[jk[u]] : make_uint2(0u, 0u);
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
+            if (u >= nu) break;
+            const int r = rr[u];
+            const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
+            const int dz = DIM == 3 ? (r / 3) - 1 : 0;
             int cxo = 0;
 #pragma unroll
             for (int qq = 1; qq < 6; ++qq) cxo += (qq < G.nb - 1 && jk[u] >= S.rb[r][qq]) ? 1 : 0;
-            ox[u] = G.xlo + cxo - G.xm;  // frame cell offset in x, |ox| <= 3
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
+            const int ox = G.xlo + cxo - G.xm;  // frame cell offset in x, |ox| <= 3
             bool keep = false;
             if (valid[u]) {
                 const float2 xy = __half22float2(as_h2(q[u].x));
-                const float x = xy.x + 2.f * (float)ox[u], y = xy.y + 2.f * (float)dy;
+                const float x = xy.x + 2.f * (float)ox, y = xy.y + 2.f * (float)dy;
                 const float z = __low2float(as_h2(q[u].y)) + 2.f * (float)dz;
                 const float ex = fmaxf(fmaxf(G.lo[0] - x, x - G.hi[0]), 0.f);
                 const float ey = fmaxf(fmaxf(G.lo[1] - y, y - G.hi[1]), 0.f);
@@ -243,13 +276,13 @@ __device__ __forceinline__ int cull_fill(TileSmem &S, const GridDev &g, const Gr
             if (keep) {
                 const int pos = kept + __popc(m & ((1u << lane) - 1u));
                 S.jall[pos] = jk[u];
-                S.code[pos] = (unsigned char)((ox[u] + 3) | ((dy + 1) << 3) | ((dz + 1) << 5));
+                S.code[pos] = (unsigned char)((ox + 3) | ((dy + 1) << 3) | ((dz + 1) << 5));
                 // the tile's own particles are the contiguous range [p0, p0 + nhome)
                 if (jk[u] >= p0 && jk[u] < p0 + nhome) S.selfpos[jk[u] - p0] = pos;
             }
             kept += __popc(m);
         }
-        cur_base += 64;
+        cur += 32 * nu;
     }
     __syncwarp();
     return kept;
@@ -257,10 +290,11 @@ __device__ __forceinline__ int cull_fill(TileSmem &S, const GridDev &g, const Gr
 
 // Stage kept candidates [w0, w0 + wc) into the window (slots past wc padded
 // far away).
-__device__ __forceinline__ void stage_window(TileSmem &S, const GridDev &g, int w0, int wc) {
+template <class C>
+__device__ __forceinline__ void stage_window(TileSmem<C> &S, const GridDev &g, int w0, int wc) {
     const int lane = threadIdx.x & 31;
 #pragma unroll 4
-    for (int k = lane; k < WIN; k += 32) {
+    for (int k = lane; k < C::WIN; k += 32) {
         __half hx, hy, hz;
         float4 f;
         if (k < wc) {
@@ -293,8 +327,8 @@ __device__ __forceinline__ void stage_window(TileSmem &S, const GridDev &g, int 
 // FP16 tests of the window (nwin words of 32) against the lane's home
 // particle; bit per kept candidate into S.S[lane][wbase + gi].  The lane's
 // own particle (window slot self_slot, or -1) is left out.
-template <int DIM>
-__device__ __forceinline__ unsigned int test_window(TileSmem &S, const Home &h, bool active, unsigned int negT,
+template <int DIM, class C>
+__device__ __forceinline__ unsigned int test_window(TileSmem<C> &S, const Home &h, bool active, unsigned int negT,
                                                     unsigned int tau, int wbase, int nwin, int self_slot) {
     const int lane = threadIdx.x & 31;
     const __half2 nT = as_h2(negT);
@@ -334,8 +368,8 @@ enum { PASS_COUNT = 0, PASS_EMIT = 1 };
 // positions p[k] (window-local candidate slots) with v[k] marking valid ones.
 // nem: the lane's words still to visit that hold at least one bit (bit gi for
 // word wbase + gi), so advancing to the next word needs no loop.
-template <int WB>
-__device__ __forceinline__ void next_bits(const TileSmem &S, int lane, int wbase, unsigned int &nem, int &gi,
+template <int WB, class C>
+__device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, int wbase, unsigned int &nem, int &gi,
                                           unsigned int &w, int (&p)[WB], bool (&v)[WB]) {
 #pragma unroll
     for (int k = 0; k < WB; ++k) {
@@ -365,8 +399,8 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 // every remaining bit is a pair j != i.  The common case (FP32 says
 // "neighbour") runs without branches; pairs the FP32 tier rejects or leaves
 // in its band go through a warp-uniform slow path.
-template <int DIM, int PASS>
-__device__ __forceinline__ void walk_window(TileSmem &S, const GridDev &g, const Home &h, int wbase,
+template <int DIM, int PASS, class C>
+__device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase,
                                             unsigned int nem, int &cnt, float &acc, int *col, long long rp,
                                             unsigned int &n32, unsigned int &n64) {
     const int lane = threadIdx.x & 31;
@@ -375,7 +409,7 @@ __device__ __forceinline__ void walk_window(TileSmem &S, const GridDev &g, const
     while (true) {
         int p[WALK_BATCH];
         bool v[WALK_BATCH];
-        next_bits<WALK_BATCH>(S, lane, wbase, nem, gi, w, p, v);
+        next_bits<WALK_BATCH, C>(S, lane, wbase, nem, gi, w, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
         float r2[WALK_BATCH];
         int jj[WALK_BATCH];
@@ -423,8 +457,8 @@ __device__ __forceinline__ void walk_window(TileSmem &S, const GridDev &g, const
 }
 
 // Set up a home group of lanes [gs, ge): frame, bounding box, band, rows.
-template <int DIM>
-__device__ __forceinline__ void group_setup(TileSmem &S, const GridDev &g, Home &h, bool act, int cy, int cz, int gs,
+template <int DIM, class C>
+__device__ __forceinline__ void group_setup(TileSmem<C> &S, const GridDev &g, Home &h, bool act, int cy, int cz, int gs,
                                             int ge, Group &G) {
     const int nx = g.nk[0];
     G.xa = __shfl_sync(0xffffffffu, h.x, gs);
@@ -452,31 +486,31 @@ __device__ __forceinline__ void group_setup(TileSmem &S, const GridDev &g, Home 
     const int mx = 1 + 2 * max(G.xm - G.xlo, G.xhi - G.xm);
     const __half t = __float2half_rn(mx < 4 ? 0.03f : 0.06f);  // FP16 band for |X| < 4 / < 8
     G.tau = h2_bits(__halves2half2(t, t));
-    group_rows<DIM>(S, g, cy, cz, G);
+    group_rows<DIM, C>(S, g, cy, cz, G);
 }
 
 // All candidates of one group against its lanes; returns false when the kept
 // list needed more than one pass (the bits in S then cover only the last).
-template <int DIM, int PASS>
-__device__ __forceinline__ bool run_group(TileSmem &S, const GridDev &g, Home &h, bool act, const Group &G,
+template <int DIM, int PASS, class C>
+__device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home &h, bool act, const Group &G,
                                           float cullT, int &cnt, float &acc, int *col, long long rp,
                                           unsigned int &n32, unsigned int &n64, int &kept_out, int p0, int nhome) {
     const int lane = threadIdx.x & 31;
-    int cur_r = 0, cur_base = 0, passes = 0, kept = 0;
+    int cur = 0, passes = 0, kept = 0;
     while (true) {
-        kept = cull_fill<DIM>(S, g, G, cullT, cur_r, cur_base, p0, nhome);
+        kept = cull_fill<DIM, C>(S, g, G, cullT, cur, p0, nhome);
         ++passes;
         const int sp = S.selfpos[lane];
-        for (int w0 = 0; w0 < kept; w0 += WIN) {
-            const int wc = min(WIN, kept - w0);
-            stage_window(S, g, w0, wc);
+        for (int w0 = 0; w0 < kept; w0 += C::WIN) {
+            const int wc = min(C::WIN, kept - w0);
+            stage_window<C>(S, g, w0, wc);
             const int nwin = (wc + 31) >> 5;
             const int self_slot = (sp >= w0 && sp < w0 + wc) ? sp - w0 : -1;
-            const unsigned int nem = test_window<DIM>(S, h, act, g.neg_t16, G.tau, w0 >> 5, nwin, self_slot);
-            walk_window<DIM, PASS>(S, g, h, w0 >> 5, nem, cnt, acc, col, rp, n32, n64);
+            const unsigned int nem = test_window<DIM, C>(S, h, act, g.neg_t16, G.tau, w0 >> 5, nwin, self_slot);
+            walk_window<DIM, PASS, C>(S, g, h, w0 >> 5, nem, cnt, acc, col, rp, n32, n64);
         }
         constexpr int NROWS = DIM == 3 ? 9 : 3;
-        if (cur_r >= NROWS) break;
+        if (cur >= S.rcum[NROWS]) break;
     }
     kept_out = kept;
     return passes == 1;
@@ -485,7 +519,8 @@ __device__ __forceinline__ bool run_group(TileSmem &S, const GridDev &g, Home &h
 // Emit the lane's kept bits (words [0, nw) of its row) in order: candidate
 // slots as 16-bit entries to stg[pos...], or (stg == nullptr) the sorted
 // indices jall[slot] to col[pos...].
-__device__ __forceinline__ void emit_bits(const TileSmem &S, int lane, int nw, long long pos, unsigned short *stg,
+template <class C>
+__device__ __forceinline__ void emit_bits(const TileSmem<C> &S, int lane, int nw, long long pos, unsigned short *stg,
                                           int *col, const int *jall) {
     unsigned int nem = 0;
     for (int q = 0; q < nw; ++q) nem |= (S.S[lane][q] != 0u ? 1u : 0u) << q;
@@ -495,7 +530,7 @@ __device__ __forceinline__ void emit_bits(const TileSmem &S, int lane, int nw, l
     while (true) {
         int p[EB];
         bool v[EB];
-        next_bits<EB>(S, lane, 0, nem, gi, w, p, v);
+        next_bits<EB, C>(S, lane, 0, nem, gi, w, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
         if (stg != nullptr) {
 #pragma unroll
@@ -518,15 +553,15 @@ __device__ __forceinline__ void emit_bits(const TileSmem &S, int lane, int nw, l
 // BATCH: tiles of several systems (td.w = system); each tile reads its
 // system's GridDev from gsys, g0 carries the shared status record and the
 // length of the concatenated sorted arrays.  Otherwise g0 is the grid.
-template <int DIM, bool BATCH>
-__global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g0, const GridDev *__restrict__ gsys,
+template <int DIM, bool BATCH, class C>
+__global__ void __launch_bounds__(32, 16) k_nnps_tile(GridDev g0, const GridDev *__restrict__ gsys,
                                                  const int4 *__restrict__ tiles,
                                                  const long long *__restrict__ ntiles_dev,
                                                  long long *__restrict__ row_ptr, int *__restrict__ col,
                                                  long long cap, float *__restrict__ rho,
                                                  unsigned long long *__restrict__ tstate, int stg_slots) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    TileSmem &S = *reinterpret_cast<TileSmem *>(smraw);
+    TileSmem<C> &S = *reinterpret_cast<TileSmem<C> *>(smraw);
     const int lane = threadIdx.x;
     const bool want_rho = rho != nullptr;
     const long long ntiles = *ntiles_dev;
@@ -560,8 +595,8 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g0, const GridDev 
             const int ge = over ? __ffs(over) - 1 : cnt_home;
             const bool act = mine && lane >= gs && lane < ge;
             Group G;
-            group_setup<DIM>(S, g, h, act, cy, cz, gs, ge, G);
-            simple &= run_group<DIM, PASS_COUNT>(S, g, h, act, G, cullT, cnt, acc, nullptr, 0, n32, n64, kept, p0,
+            group_setup<DIM, C>(S, g, h, act, cy, cz, gs, ge, G);
+            simple &= run_group<DIM, PASS_COUNT, C>(S, g, h, act, G, cullT, cnt, acc, nullptr, 0, n32, n64, kept, p0,
                                                  cnt_home);
             ++groups;
             gs = ge;
@@ -581,8 +616,8 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g0, const GridDev 
         // output out in shared memory before it needs its CSR offset, so the
         // wait on earlier tiles overlaps that work.
         const bool staged = simple && col != nullptr && agg <= stg_slots;
-        unsigned short *stg = reinterpret_cast<unsigned short *>(&S.pw[0]);
-        if (staged) emit_bits(S, lane, mine ? (kept + 31) >> 5 : 0, rstart, stg, nullptr, nullptr);
+        unsigned short *stg = reinterpret_cast<unsigned short *>(&S.code[0]);
+        if (staged) emit_bits<C>(S, lane, mine ? (kept + 31) >> 5 : 0, rstart, stg, nullptr, nullptr);
         const long long pre = look_back_resolve(tstate, t, agg, &g0.status->flags);
         const bool wc = col != nullptr && pre + agg <= cap;
         if (col != nullptr && !wc && lane == 0) atomicOr(&g0.status->flags, ST_CAPACITY);
@@ -599,7 +634,7 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g0, const GridDev 
             __syncwarp();
         } else if (simple) {
             // segment larger than the staging area: rows straight to col
-            emit_bits(S, lane, mine ? (kept + 31) >> 5 : 0, pre + rstart, nullptr, col, S.jall);
+            emit_bits<C>(S, lane, mine ? (kept + 31) >> 5 : 0, pre + rstart, nullptr, col, S.jall);
         } else {
             // emit pass: same decisions again, written straight to the rows
             int ecnt = 0;
@@ -611,9 +646,9 @@ __global__ void __launch_bounds__(32, 12) k_nnps_tile(GridDev g0, const GridDev 
                 const int ge = over ? __ffs(over) - 1 : cnt_home;
                 const bool act = mine && lane >= gs && lane < ge;
                 Group G;
-                group_setup<DIM>(S, g, h, act, cy, cz, gs, ge, G);
+                group_setup<DIM, C>(S, g, h, act, cy, cz, gs, ge, G);
                 int kk;
-                run_group<DIM, PASS_EMIT>(S, g, h, act, G, cullT, ecnt, dummy, col, pre + rstart, e32, e64, kk, p0,
+                run_group<DIM, PASS_EMIT, C>(S, g, h, act, G, cullT, ecnt, dummy, col, pre + rstart, e32, e64, kk, p0,
                                           cnt_home);
                 gs = ge;
             }
@@ -656,9 +691,53 @@ __global__ void k_cell_x(GridDev g, const int *__restrict__ scell, int *__restri
         sx[s] = scell[s] % g.nk[0];
 }
 
-}  // namespace
+// The staged output area (code, pw, f32, then the launch's extra dynamic
+// shared memory) must be one contiguous range.
+template <class C>
+constexpr bool staging_contiguous() {
+    return offsetof(TileSmem<C>, pw) == offsetof(TileSmem<C>, code) + sizeof(TileSmem<C>::code) &&
+           offsetof(TileSmem<C>, f32) == offsetof(TileSmem<C>, pw) + sizeof(TileSmem<C>::pw) &&
+           sizeof(TileSmem<C>) == offsetof(TileSmem<C>, f32) + sizeof(TileSmem<C>::f32);
+}
+static_assert(staging_contiguous<TileSparse>() && staging_contiguous<TileDense>(), "staging layout");
 
-size_t tile_smem_bytes() { return sizeof(TileSmem); }
+template <class C>
+cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
+                         long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
+                         unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s) {
+    using SM = TileSmem<C>;
+    const size_t sb = sizeof(SM) + (size_t)extra_smem;
+    const bool batch = gsys != nullptr;
+    const int ki = (g.dim == 2 ? 0 : 2) + (batch ? 1 : 0);
+    auto kern = ki == 0 ? k_nnps_tile<2, false, C> : ki == 1 ? k_nnps_tile<2, true, C>
+              : ki == 2 ? k_nnps_tile<3, false, C> : k_nnps_tile<3, true, C>;
+    // The shared-memory limit is set once per kernel, to the largest launch
+    // any option allows (launches from several threads then never see a
+    // limit another thread lowered).
+    static std::once_flag once[4];
+    static cudaError_t once_err[4];
+    std::call_once(once[ki], [&] {
+        once_err[ki] = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(SM) + TILE_MAX_EXTRA_SMEM));
+    });
+    if (once_err[ki] != cudaSuccess) return once_err[ki];
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, sb);
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)sm_count * per_sm;
+    if (blocks > ntiles_max) blocks = ntiles_max;
+    if (blocks < 1) blocks = 1;
+    cudaError_t e =
+        cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int stg_slots = (int)((SM::staging_bytes() + (size_t)extra_smem) / 2);
+    ProfScope ps(TAG_FUSED, s);
+    note_launch(1);
+    kern<<<(unsigned)blocks, 32, sb, s>>>(g, gsys, tiles, ntiles_dev, row_ptr, col, cap, rho, tstate, stg_slots);
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 // Build the tile list of a binned grid.  tcount: int[nrow], toff: int64[nrow+1],
 // tiles: int4[ntiles_max] with ntiles_max = n / 32 + nrow.
@@ -685,53 +764,38 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *
 // ntiles_dev: device pointer to the tile count (the last entry of the row
 // tile offsets); ntiles_max bounds it (sizes the look-back state).
 // gsys != nullptr: batch tiles (td.w = system), g then carries the status
-// record and the total particle count.  extra_smem: dynamic shared memory
-// beyond TileSmem, all of it staging area for the tile's output.
+// record and the total particle count.  v: shared-memory shape and extra
+// dynamic shared memory (all of it staging area for the tile's output).
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
-                             unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s) {
-    if (extra_smem < 0 || extra_smem > TILE_MAX_EXTRA_SMEM) return cudaErrorInvalidValue;
-    const size_t sb = sizeof(TileSmem) + (size_t)extra_smem;
-    const bool batch = gsys != nullptr;
-    const int ki = (g.dim == 2 ? 0 : 2) + (batch ? 1 : 0);
-    auto kern = ki == 0 ? k_nnps_tile<2, false> : ki == 1 ? k_nnps_tile<2, true>
-              : ki == 2 ? k_nnps_tile<3, false> : k_nnps_tile<3, true>;
-    // The shared-memory limit is set once per kernel, to the largest launch
-    // any option allows (launches from several threads then never see a
-    // limit another thread lowered).
-    static std::once_flag once[4];
-    static cudaError_t once_err[4];
-    std::call_once(once[ki], [&] {
-        once_err[ki] = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(sizeof(TileSmem) + TILE_MAX_EXTRA_SMEM));
-    });
-    if (once_err[ki] != cudaSuccess) return once_err[ki];
-    cudaError_t e;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, sb);
-    if (per_sm < 1) per_sm = 1;
-    long long blocks = (long long)sm_count * per_sm;
-    if (blocks > ntiles_max) blocks = ntiles_max;
-    if (blocks < 1) blocks = 1;
-    e = cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-    const int stg_slots = (int)((sizeof(TileSmem::pw) + sizeof(TileSmem::f32) + (size_t)extra_smem) / 2);
-    ProfScope ps(TAG_FUSED, s);
-    note_launch(1);
-    kern<<<(unsigned)blocks, 32, sb, s>>>(g, gsys, tiles, ntiles_dev, row_ptr, col, cap, rho, tstate, stg_slots);
-    return cudaGetLastError();
+                             unsigned long long *tstate, TileLaunch v, int sm_count, cudaStream_t s) {
+    if (v.extra < 0 || v.extra > TILE_MAX_EXTRA_SMEM || (v.shape != TILE_SPARSE && v.shape != TILE_DENSE))
+        return cudaErrorInvalidValue;
+    if (v.shape == TILE_DENSE)
+        return launch_shape<TileDense>(g, gsys, tiles, ntiles_dev, ntiles_max, row_ptr, col, cap, rho, tstate,
+                                       v.extra, sm_count, s);
+    return launch_shape<TileSparse>(g, gsys, tiles, ntiles_dev, ntiles_max, row_ptr, col, cap, rho, tstate, v.extra,
+                                    sm_count, s);
 }
 
-// Extra staging bytes for a grid whose rows hold about `nbr` neighbours on
-// average: enough for a tile of 32 such rows with 15% to spare, in
-// steps of 2 KB (each step costs occupancy), none when the window buffers
-// suffice.
-int tile_extra_smem(double nbr) {
+// Shape and staging for a grid whose rows hold about `nbr` neighbours on
+// average.  Up to 90 neighbours the candidates kept per group stay well
+// under the sparse shape's 768; beyond, the dense shape.  Extra staging only
+// when a tile of 32 such rows (with 15% to spare) needs more than 1.5 times
+// the built-in area: measured on 1M and 8M particle sets, the occupancy it
+// costs outweighs the coalesced output for the tiles just above the area.
+TileLaunch tile_choose(double nbr, int shape) {
+    TileLaunch v;
+    v.shape = shape >= 0 ? shape : (nbr < 90.0 ? TILE_SPARSE : TILE_DENSE);
+    const double have = (double)(v.shape == TILE_DENSE ? TileSmem<TileDense>::staging_bytes()
+                                                        : TileSmem<TileSparse>::staging_bytes());
     const double want = 32.0 * nbr * 1.15 * 2.0;  // bytes of 16-bit slots
-    const double have = (double)(sizeof(TileSmem::pw) + sizeof(TileSmem::f32));
-    if (want <= have) return 0;
-    int extra = (int)((want - have + 2047.0) / 2048.0) * 2048;
-    return extra > 16384 ? 16384 : extra;
+    v.extra = 0;
+    if (want > 1.5 * have) {
+        v.extra = (int)((want - have + 2047.0) / 2048.0) * 2048;
+        if (v.extra > 16384) v.extra = 16384;
+    }
+    return v;
 }
 
 }  // namespace sph

@@ -64,6 +64,7 @@ class sph_batch_out(ctypes.Structure):
 class sph_batch_stats(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int64), ("graph_captures", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("tuned_staging", ctypes.c_int32), ("tuned_candidates", ctypes.c_int32),
+                ("tuned_shape", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("fp32_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64)]
 
 
@@ -189,6 +190,7 @@ def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=Non
 
 SPH_OPT_FUSED = 1
 SPH_OPT_STAGING = 2
+SPH_OPT_TILE_SHAPE = 3
 
 
 def sph_grid_set_option(grid, option, value):

@@ -264,3 +264,21 @@ def test_nonfinite_in_tail_rejected(sph, where):
     with pytest.raises(sph.SphError) as ei:
         sph.Grid(torch.from_numpy(xyz).cuda(), 0.05)
     assert ei.value.code == sph.SPH_ERR_INVALID
+
+
+@pytest.mark.parametrize("shape,staging", [(0, 0), (1, 0), (0, 4096), (1, 2048)])
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "dambreak_small", "random3d_dense"])
+def test_tile_shapes_and_staging(sph, case, shape, staging):
+    """Both shared-memory shapes of the tile search, with and without extra
+    staging, give the oracle's lists and densities."""
+    if case == "random3d_dense":
+        xyz, h = W.random_uniform(20000, 3, 21), 0.05  # ~110 neighbours per particle
+    else:
+        xyz, h = CASES[case]()
+    x = torch.from_numpy(np.ascontiguousarray(xyz)).cuda()
+    g = sph.Grid(x, h, 2 * h, order=0)
+    sph.sph_grid_set_option(g.handle, sph.SPH_OPT_TILE_SHAPE, shape)
+    sph.sph_grid_set_option(g.handle, sph.SPH_OPT_STAGING, staging)
+    rp, col, rho = g.query()
+    out = dict(rp=rp.cpu().numpy(), col=col.cpu().numpy(), rho=rho.cpu().numpy(), orig=g.orig_id().cpu().numpy())
+    check_against_oracle(out, xyz, h, 2 * h, 0)
