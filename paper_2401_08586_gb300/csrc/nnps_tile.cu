@@ -71,7 +71,7 @@ struct TileSmem {
     unsigned int S[TW][C::NWORD + 1];
     int jall[C::CMAX];  // kept candidates: sorted index
     int selfpos[TW];    // kept slot of each lane's own particle (-1: not in this fill)
-    int rstart[9], rlen[9], rcum[10], rb[9][8];  // candidate rows: start, length, flat prefix, cell bounds
+    int rstart[9], rlen[9], rcum[10], pad[4];  // candidate rows: start, length, flat prefix
     // code, pw and f32 come last and are contiguous with any extra dynamic
     // shared memory of the launch: after the last window they hold the tile's
     // staged output (16-bit kept-candidate slots), stg_slots of them
@@ -92,9 +92,10 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // P(R) of Eq. 3 without alpha_d, branch-free: 2/3 - R^2 + R^3/2 on [0, 1),
-// (2 - R)^3 / 6 on [1, 2), 0 beyond.
+// (2 - R)^3 / 6 on [1, 2).  Only called for neighbours (R < 2); other values
+// are discarded by the caller.
 __device__ __forceinline__ float w_poly_bf(float R) {
-    const float t = fmaxf(2.f - R, 0.f);
+    const float t = 2.f - R;
     const float w2 = t * t * t * (1.f / 6.f);
     const float w1 = fmaf(R * R, fmaf(0.5f, R, -1.f), 2.f / 3.f);
     return R < 1.f ? w1 : w2;
@@ -170,43 +171,44 @@ struct Home {
 
 // One home group: its cells, frame and candidate rows.
 struct Group {
-    int xa, xb, xm, xlo, xhi, nb;  // nb = cell boundaries per candidate row
+    int xa, xb, xm, xlo, xhi;      // home cells [xa, xb], middle xm, candidate cells [xlo, xhi]
     float lo[3], hi[3];            // bounding box of the group's particles (frame, FP32)
     unsigned int tau;              // FP16 band (half2 bits)
 };
 
-// Candidate row table of a group (cells [xa, xb] of row (cy, cz)).
+// Candidate row table of a group: for each of the 3^d rows of cells around
+// the group's row (cy, cz), the sorted range of cells [xlo, xhi].
 template <int DIM, class C>
 __device__ __forceinline__ void group_rows(TileSmem<C> &S, const GridDev &g, int cy, int cz, const Group &G) {
     constexpr int NROWS = DIM == 3 ? 9 : 3;
     const int lane = threadIdx.x & 31;
     const int nx = g.nk[0], ny = g.nk[1], nz = g.nk[2];
-    for (int e = lane; e < 9 * 8; e += 32) {
-        const int r = e >> 3, k = e & 7;
-        int v = -1;
-        if (r < NROWS && k < G.nb) {
-            const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
-            const int dz = DIM == 3 ? (r / 3) - 1 : 0;
-            const int yy = cy + dy, zz = cz + dz;
-            if (yy >= 0 && yy < ny && zz >= 0 && zz < nz) v = g.cell_start[((long long)zz * ny + yy) * nx + G.xlo + k];
-        }
-        S.rb[r][k] = v;
+    // lane 2r + e loads the start (e = 0) or end (e = 1) of row r
+    int v = -1;
+    const int r = lane >> 1, e = lane & 1;
+    if (r < NROWS) {
+        const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
+        const int dz = DIM == 3 ? (r / 3) - 1 : 0;
+        const int yy = cy + dy, zz = cz + dz;
+        if (yy >= 0 && yy < ny && zz >= 0 && zz < nz)
+            v = g.cell_start[((long long)zz * ny + yy) * nx + (e ? G.xhi + 1 : G.xlo)];
     }
-    __syncwarp();
+    const int vend = __shfl_down_sync(0xffffffffu, v, 1);
     int len = 0;
-    if (lane < 9) {
-        const int r = lane;
-        const int a = S.rb[r][0];
-        S.rstart[r] = a >= 0 ? a : 0;
-        len = a >= 0 ? S.rb[r][G.nb - 1] - a : 0;
-        S.rlen[r] = len;
+    if (lane < 2 * NROWS && e == 0) {
+        S.rstart[r] = v >= 0 ? v : 0;
+        len = v >= 0 ? vend - v : 0;
     }
+    // rows to lanes 0 .. NROWS-1
+    len = __shfl_sync(0xffffffffu, len, 2 * (lane < NROWS ? lane : 0));
+    if (lane >= NROWS) len = 0;
+    if (lane < NROWS) S.rlen[lane] = len;
     // flat index of the candidates: rcum[r] = candidates in rows before r
     int inc = len;
 #pragma unroll
     for (int o = 1; o < 16; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
+        const int up = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += up;
     }
     if (lane < 9) S.rcum[lane + 1] = inc;
     if (lane == 0) S.rcum[0] = 0;
@@ -234,7 +236,7 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
     int kept = 0;
     while (cur < total && kept + 32 <= C::CMAX) {
         const int nu = kept + 32 * U <= C::CMAX ? U : 1;  // warp-uniform
-        int jk[U], rr[U];
+        int jk[U], rr[U], cx[U];
         bool valid[U];
         uint2 q[U];
 #pragma unroll
@@ -251,6 +253,7 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
             rr[u] = r;
             jk[u] = S.rstart[r] + (k - base);
             q[u] = valid[u] ? g.rel16[jk[u]] : make_uint2(0u, 0u);
+            cx[u] = valid[u] ? g.scell_x[jk[u]] : G.xm;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -258,10 +261,7 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
             const int r = rr[u];
             const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
             const int dz = DIM == 3 ? (r / 3) - 1 : 0;
-            int cxo = 0;
-#pragma unroll
-            for (int qq = 1; qq < 6; ++qq) cxo += (qq < G.nb - 1 && jk[u] >= S.rb[r][qq]) ? 1 : 0;
-            const int ox = G.xlo + cxo - G.xm;  // frame cell offset in x, |ox| <= 3
+            const int ox = cx[u] - G.xm;  // frame cell offset in x, |ox| <= 3
             bool keep = false;
             if (valid[u]) {
                 const float2 xy = __half22float2(as_h2(q[u].x));
@@ -400,7 +400,7 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 // "neighbour") runs without branches; pairs the FP32 tier rejects or leaves
 // in its band go through a warp-uniform slow path.
 template <int DIM, int PASS, class C>
-__device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase,
+__device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase, int nwin,
                                             unsigned int nem, int &cnt, float &acc, int *col, long long rp,
                                             unsigned int &n32, unsigned int &n64) {
     const int lane = threadIdx.x & 31;
@@ -449,9 +449,12 @@ __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, co
             for (int k = 0; k < WALK_BATCH; ++k) {
                 const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
                 acc += in[k] ? wk : 0.f;
-                cnt += in[k] ? 1 : 0;
             }
         }
+    }
+    if (PASS == PASS_COUNT) {
+        // the neighbours of this window: its bits that survived the re-decision
+        for (int q = 0; q < nwin; ++q) cnt += __popc(S.S[lane][wbase + q]);
     }
     __syncwarp();
 }
@@ -466,7 +469,6 @@ __device__ __forceinline__ void group_setup(TileSmem<C> &S, const GridDev &g, Ho
     G.xm = (G.xa + G.xb) >> 1;
     G.xlo = max(G.xa - 1, 0);
     G.xhi = min(G.xb + 1, nx - 1);
-    G.nb = G.xhi - G.xlo + 2;
     const uint2 q = g.rel16[min(h.i, g.n - 1)];
     const float4 r = g.rel32[min(h.i, g.n - 1)];
     const float sx = 2.f * (float)(h.x - G.xm);
@@ -507,7 +509,7 @@ __device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home
             const int nwin = (wc + 31) >> 5;
             const int self_slot = (sp >= w0 && sp < w0 + wc) ? sp - w0 : -1;
             const unsigned int nem = test_window<DIM, C>(S, h, act, g.neg_t16, G.tau, w0 >> 5, nwin, self_slot);
-            walk_window<DIM, PASS, C>(S, g, h, w0 >> 5, nem, cnt, acc, col, rp, n32, n64);
+            walk_window<DIM, PASS, C>(S, g, h, w0 >> 5, nwin, nem, cnt, acc, col, rp, n32, n64);
         }
         constexpr int NROWS = DIM == 3 ? 9 : 3;
         if (cur >= S.rcum[NROWS]) break;
