@@ -76,13 +76,11 @@ __global__ void k_advance(GridDev g, const int *__restrict__ scell, const double
             }
             c = (cc[2] * g.nk[1] + cc[1]) * g.nk[0] + cc[0];
             rel64u[i] = make_double4(a[0], a[1], a[2], 0.0);
-            const __half2 xy = __halves2half2(__double2half(a[0]), __double2half(a[1]));
-            const __half2 z0 = __halves2half2(__double2half(a[2]), __double2half(0.0));
             uint2 q;
-            q.x = *reinterpret_cast<const unsigned int *>(&xy);
-            q.y = *reinterpret_cast<const unsigned int *>(&z0);
+            float4 f;
+            round_rel(a, q, f);
             rel16u[i] = q;
-            rel32u[i] = make_float4(__double2float_rn(a[0]), __double2float_rn(a[1]), __double2float_rn(a[2]), 0.f);
+            rel32u[i] = f;
         }
         if (__any_sync(0xffffffffu, out) && lane == 0) atomicOr(&g.status->flags, ST_OUT_OF_BOX);
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&g.status->flags, ST_NONFINITE);

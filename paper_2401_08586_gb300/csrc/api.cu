@@ -56,6 +56,14 @@ static GridDev make_dev(sph_grid_s *g) {
     d.ncell = g->ncell;
     d.hc = g->hc;
     d.two_over_hc = 2.0 / g->hc;
+    // one-FMA binning when every coordinate of the grid lies within 2^17 u of
+    // the origin (|x| 2/h_c <= 2^17 for x in [lo, lo + n h_c])
+    d.fma_bin = 1;
+    for (int k = 0; k < 3; ++k) {
+        d.neg_lo_t[k] = -g->lo[k] * d.two_over_hc;
+        const double far = fmax(fabs(g->lo[k]), fabs(g->lo[k] + g->nk[k] * g->hc)) * d.two_over_hc;
+        if (!(far <= 131072.0)) d.fma_bin = 0;
+    }
     d.cell_start = P<int>(g->cell_start);
     d.rel16 = P<uint2>(g->rel16);
     d.rel32 = P<float4>(g->rel32);
@@ -175,7 +183,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
             (rc = ensure(g->slot, nn * sizeof(int), s)) || (rc = ensure(g->orig_id, nn * sizeof(int), s)) ||
             (rc = ensure(g->rank, nn * sizeof(int), s)) || (rc = ensure(g->scell, nn * sizeof(int), s)) ||
             (rc = ensure(g->scan_tmp, scan_tmp_bytes(big + 1), s)) ||
-            (rc = ensure(g->big_list, big * sizeof(int), s)))
+            (rc = ensure(g->big_list, big * sizeof(int), s)) || (rc = ensure(g->scell_x, nn * sizeof(int), s)))
             break;
         if (p->precision == SPH_PREC_FP16_RCLL) {
             if ((rc = ensure(g->rel16, nn * sizeof(uint2), s)) || (rc = ensure(g->rel32, nn * sizeof(float4), s)) ||
@@ -195,7 +203,8 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
         cudaError_t e = launch_hash_scatter_convert(
             d, xyz, (int)n, dim, p->precision, P<int>(g->cnt), P<int>(g->cid), P<int>(g->slot),
             P<int>(g->cell_start), P<int>(g->orig_id), P<int>(g->rank), P<int>(g->scell), P<uint2>(g->rel16),
-            P<float4>(g->rel32), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4>(g->x64), g->scan_tmp.p, P<int>(g->big_list),
+            P<float4>(g->rel32), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4>(g->x64), P<int>(g->scell_x),
+            g->scan_tmp.p, P<int>(g->big_list),
             &P<DevStatus>(g->status)->big_cells, p->have_box, g->sm_count, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -261,6 +270,7 @@ extern "C" int sph_advance(sph_grid_t grid, const double *xyz_new, const double 
                                   P<int>(g->slot), P<int>(g->cell_start), P<int>(g->orig_id), P<int>(g->rank),
                                   P<int>(g->scell), P<uint2>(g->rel16), P<float4>(g->rel32), P<uint2>(g->rel16u),
                                   P<float4>(g->rel32u), P<double4>(g->rel64u), P<double4>(g->rel64), nullptr,
+                                  P<int>(g->scell_x),
                                   g->scan_tmp.p, P<int>(g->big_list), &P<DevStatus>(g->status)->big_cells,
                                   g->sm_count, s));
     g->xyz = xyz_new;
@@ -305,13 +315,13 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         // single pass, one warp per 32-particle row tile, look-back across tiles
         const long long nrow = (long long)g->nk[1] * g->nk[2];
         const long long ntiles_max = n / 32 + nrow + 1;
-        SPH_TRY(ensure(g->scell_x, n * sizeof(int), s));
         SPH_TRY(ensure(g->tcount, nrow * sizeof(int), s));
         SPH_TRY(ensure(g->toff, (nrow + 1) * sizeof(long long), s));
         SPH_TRY(ensure(g->tiles, ntiles_max * sizeof(int4), s));
         SPH_TRY(ensure(g->tstate, ntiles_max * sizeof(unsigned long long), s));
         d = make_dev(g);
-        SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), P<int>(g->tcount), P<long long>(g->toff),
+        SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), false, P<int>(g->tcount),
+                              P<long long>(g->toff),
                               g->scan_tmp.p, P<int4>(g->tiles), g->sm_count, s));
         // neighbours per particle: the last measured value, else the
         // uniform-density estimate (particles per cell x the search sphere's

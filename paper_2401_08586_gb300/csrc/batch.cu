@@ -118,13 +118,11 @@ __global__ void k_batch_hash(const BinSys *__restrict__ sys, const long long *__
             }
             if (out && S.check_box) atomicOr(&st->flags, ST_OUT_OF_BOX);
             c = S.cell_base + (cc[2] * S.nk[1] + cc[1]) * S.nk[0] + cc[0];
-            const __half2 xy = __halves2half2(__double2half(a[0]), __double2half(a[1]));
-            const __half2 z0 = __halves2half2(__double2half(a[2]), __double2half(0.0));
             uint2 q;
-            q.x = *reinterpret_cast<const unsigned int *>(&xy);
-            q.y = *reinterpret_cast<const unsigned int *>(&z0);
+            float4 f;
+            round_rel(a, q, f);
             rel16u[I] = q;
-            rel32u[I] = make_float4(__double2float_rn(a[0]), __double2float_rn(a[1]), __double2float_rn(a[2]), 0.f);
+            rel32u[I] = f;
         }
         const unsigned int peers = __match_any_sync(0xffffffffu, c);
         const int leader = __ffs(peers) - 1;

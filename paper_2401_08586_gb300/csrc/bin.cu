@@ -113,23 +113,25 @@ __global__ void k_hash(const double *__restrict__ xyz, int n, int dim, GridDev g
         if (live) {
             int cc[3] = {0, 0, 0};
             double a[3] = {0.0, 0.0, 0.0};
-            bool out = false;
-            for (int k = 0; k < dim; ++k) {
-                cc[k] = rel_axis(xyz[i * dim + k], g.lo[k], g.two_over_hc, g.nk[k], a[k]);
-                out |= fabs(a[k]) > 1.0 + 1e-6;
+            if (g.fma_bin) {
+                for (int k = 0; k < dim; ++k)
+                    cc[k] = rel_axis_fma(xyz[i * dim + k], g.neg_lo_t[k], g.two_over_hc, g.nk[k], a[k]);
+            } else {
+                for (int k = 0; k < dim; ++k)
+                    cc[k] = rel_axis(xyz[i * dim + k], g.lo[k], g.two_over_hc, g.nk[k], a[k]);
             }
-            if (out && check_box) atomicOr(&g.status->flags, ST_OUT_OF_BOX);
+            if (check_box) {
+                bool out = false;
+                for (int k = 0; k < dim; ++k) out |= fabs(a[k]) > 1.0 + 1e-6;
+                if (out) atomicOr(&g.status->flags, ST_OUT_OF_BOX);
+            }
             c = (cc[2] * g.nk[1] + cc[1]) * g.nk[0] + cc[0];
             if (PREC == SPH_PREC_FP16_RCLL) {
-                // rounded once, to nearest even, from the FP64 value
-                const __half2 xy = __halves2half2(__double2half(a[0]), __double2half(a[1]));
-                const __half2 z0 = __halves2half2(__double2half(a[2]), __double2half(0.0));
                 uint2 q;
-                q.x = *reinterpret_cast<const unsigned int *>(&xy);
-                q.y = *reinterpret_cast<const unsigned int *>(&z0);
+                float4 f;
+                round_rel(a, q, f);
                 rel16u[i] = q;
-                rel32u[i] = make_float4(__double2float_rn(a[0]), __double2float_rn(a[1]),
-                                        __double2float_rn(a[2]), 0.f);
+                rel32u[i] = f;
             }
         }
         // Lanes with the same cell add to its counter once.
@@ -160,12 +162,14 @@ __global__ void k_convert(int n, int dim, GridDev g, const int *__restrict__ cid
                           int *__restrict__ rank, int *__restrict__ scell, uint2 *__restrict__ rel16,
                           float4 *__restrict__ rel32, const uint2 *__restrict__ rel16u,
                           const float4 *__restrict__ rel32u, const double4 *__restrict__ rel64u,
-                          double4 *__restrict__ rel64, double4 *__restrict__ x64) {
+                          double4 *__restrict__ rel64, double4 *__restrict__ x64, int *__restrict__ scell_x) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
         const int i = g.orig_id[s];
         rank[i] = (int)s;
-        scell[s] = cid_in[i];
+        const int c = cid_in[i];
+        scell[s] = c;
+        if (scell_x != nullptr) scell_x[s] = c % g.nk[0];
         if (PREC == SPH_PREC_FP64_CLL) {
             double x[3] = {0.0, 0.0, 0.0};
             for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];
@@ -206,8 +210,8 @@ cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st
 cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
                                  int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
                                  const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,
-                                 double4 *x64, void *scan_tmp, int *big_list, unsigned int *big_count, int sm_count,
-                                 cudaStream_t s) {
+                                 double4 *x64, int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
+                                 int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
     cudaError_t e = exclusive_scan_i32(cnt, cell_start, g.ncell, scan_tmp, s);
@@ -223,17 +227,17 @@ cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int
     note_launch(1);
     if (prec == SPH_PREC_FP16_RCLL)
         k_convert<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, rel16, rel32, rel16u,
-                                                            rel32u, rel64u, rel64, nullptr);
+                                                            rel32u, rel64u, rel64, nullptr, scell_x);
     else
         k_convert<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, nullptr, nullptr, nullptr,
-                                                           nullptr, nullptr, nullptr, x64);
+                                                           nullptr, nullptr, nullptr, x64, scell_x);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec,
                                         int *cnt, int *cid, int *slot, int *cell_start, int *orig_id,
                                         int *rank, int *scell, uint2 *rel16, float4 *rel32, uint2 *rel16u,
-                                        float4 *rel32u, double4 *x64, void *scan_tmp, int *big_list,
+                                        float4 *rel32u, double4 *x64, int *scell_x, void *scan_tmp, int *big_list,
                                         unsigned int *big_count, int check_box, int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
@@ -254,7 +258,8 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
     // a fresh binning leaves the FP64 relative coordinates (kept for time
     // steps) to be derived again on the next step
     return launch_order_convert(g, n, dim, prec, cnt, cid, slot, cell_start, orig_id, rank, scell, rel16, rel32,
-                                rel16u, rel32u, nullptr, nullptr, x64, scan_tmp, big_list, big_count, sm_count, s);
+                                rel16u, rel32u, nullptr, nullptr, x64, scell_x, scan_tmp, big_list, big_count,
+                                sm_count, s);
 }
 
 }  // namespace sph

@@ -13,16 +13,16 @@ cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec, int *cnt,
                                         int *cid, int *slot, int *cell_start, int *orig_id, int *rank, int *scell,
                                         uint2 *rel16, float4 *rel32, uint2 *rel16u, float4 *rel32u, double4 *x64,
-                                        void *scan_tmp, int *big_list, unsigned int *big_count, int check_box,
-                                        int sm_count, cudaStream_t s);
+                                        int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
+                                        int check_box, int sm_count, cudaStream_t s);
 // Scan of the cell histogram, scatter, per-cell sort and the gather of the
 // input-order arrays (cid, rel16u, rel32u and, if not NULL, rel64u) into
 // cell order: the second half of binning, shared with the time step.
 cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
                                  int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
                                  const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,
-                                 double4 *x64, void *scan_tmp, int *big_list, unsigned int *big_count, int sm_count,
-                                 cudaStream_t s);
+                                 double4 *x64, int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
+                                 int sm_count, cudaStream_t s);
 cudaError_t launch_scatter(int n, const int *cell_start, const int *cid, const int *slot, int *orig_id,
                            int sm_count, cudaStream_t s);
 
@@ -65,8 +65,10 @@ cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, lo
                               unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);
 
 // Single-pass search, one warp per row tile (nnps_tile.cu).
-cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
-                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
+// need_cell_x: compute scell_x from scell first (binning already wrote it
+// for grids; the no-allocation path keeps its own copy).
+cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
+                         long long *toff, void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
 // Shared-memory shape of a tile-search launch: TILE_SPARSE (768 kept
 // candidates per pass, 16 warps per SM) or TILE_DENSE (1024, 13 per SM), and
 // extra dynamic shared memory for output staging.

@@ -743,8 +743,8 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
 
 // Build the tile list of a binned grid.  tcount: int[nrow], toff: int64[nrow+1],
 // tiles: int4[ntiles_max] with ntiles_max = n / 32 + nrow.
-cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *tcount, long long *toff,
-                         void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s) {
+cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
+                         long long *toff, void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s) {
     const long long nrow = (long long)g.nk[1] * g.nk[2];
     const int nt = 256;
     long long b = (nrow + nt - 1) / nt;
@@ -754,8 +754,8 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, int *
     if (bn > (long long)sm_count * 16) bn = (long long)sm_count * 16;
     if (bn < 1) bn = 1;
     ProfScope ps(TAG_SCAN, s);
-    note_launch(3);
-    k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
+    note_launch(need_cell_x ? 3 : 2);
+    if (need_cell_x) k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
     k_row_tiles_count<<<(unsigned)b, nt, 0, s>>>(g, tcount);
     cudaError_t e = exclusive_scan_i64(tcount, toff, nrow, scan_tmp, s);
     if (e != cudaSuccess) return e;

@@ -46,6 +46,8 @@ struct GridDev {
     double lo[3];
     double hc;           // h_c
     double two_over_hc;  // 2 / h_c: FP64 units -> u
+    double neg_lo_t[3];  // -lo * 2 / h_c (binning in one FMA, when fma_bin)
+    int fma_bin;         // 1: every coordinate is within 2^17 u of the origin
     const int *cell_start;
     const uint2 *rel16;   // per sorted particle: half x_rel, y_rel | z_rel, 0
     const float4 *rel32;  // per sorted particle: x_rel, y_rel, z_rel, 0
@@ -98,12 +100,36 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double hc, int nk
 // i.e. at most 2^-31 u at the 2^20-cell limit, below the 2^-29 u margin that
 // the cell size kh (1 + 2^-30) leaves, so every pair closer than kh sits in
 // the same or adjacent cells.
-__device__ __forceinline__ int rel_axis(double x, double lo, double two_over_hc, int nk, double &a) {
-    const double s = __dmul_rn(__dsub_rn(x, lo), two_over_hc);
+__device__ __forceinline__ int rel_axis_s(double s, int nk, double &a) {
     int c = __double2int_rd(s) >> 1;  // floor(floor(s) / 2) = floor(s / 2); saturating conversion
     c = min(max(c, 0), nk - 1);
     a = __dsub_rn(s, (double)(2 * c + 1));
     return c;
+}
+
+__device__ __forceinline__ int rel_axis(double x, double lo, double two_over_hc, int nk, double &a) {
+    return rel_axis_s(__dmul_rn(__dsub_rn(x, lo), two_over_hc), nk, a);
+}
+
+// The same with s = fma(x, 2 / h_c, -lo 2 / h_c) in one rounding (plus the
+// roundings of the two constants): |s - exact| <= 2^-53 (|s| + |x| 2/h_c +
+// |lo| 2/h_c), at most 2^-33.4 u when |x| and |lo| are at most 2^17 u, which
+// the caller checks for the whole grid before choosing this form.
+__device__ __forceinline__ int rel_axis_fma(double x, double neg_lo_t, double two_over_hc, int nk, double &a) {
+    return rel_axis_s(__fma_rn(x, two_over_hc, neg_lo_t), nk, a);
+}
+
+// The stored relative coordinates: FP32 rounded once from the FP64 value,
+// FP16 rounded from the FP32 value.  The second rounding adds at most 2^-25
+// u to the FP16 coordinate's error (2^-12 u for |x_rel| <= 1), far inside the
+// FP16 band's margin.
+__device__ __forceinline__ void round_rel(const double a[3], uint2 &q16, float4 &f32) {
+    const float f0 = __double2float_rn(a[0]), f1 = __double2float_rn(a[1]), f2 = __double2float_rn(a[2]);
+    const __half2 xy = __floats2half2_rn(f0, f1);
+    const __half2 z0 = __floats2half2_rn(f2, 0.f);
+    q16.x = *reinterpret_cast<const unsigned int *>(&xy);
+    q16.y = *reinterpret_cast<const unsigned int *>(&z0);
+    f32 = make_float4(f0, f1, f2, 0.f);
 }
 
 // What another translation unit of the library may see of a grid
