@@ -687,6 +687,46 @@ __global__ void k_row_tiles_write(GridDev g, const long long *__restrict__ toff,
     }
 }
 
+// Grids of nrow <= ROWS_SMALL_MAX rows: tiles per row and their exclusive
+// scan in one single-block launch (each thread a contiguous run of rows).
+__global__ void __launch_bounds__(1024) k_row_tiles_scan_small(GridDev g, long long *__restrict__ toff) {
+    __shared__ long long wsum[32];
+    const long long nrow = (long long)g.nk[1] * g.nk[2];
+    const long long per = (nrow + 1023) / 1024;
+    const long long a = (long long)threadIdx.x * per, b = a + per < nrow ? a + per : nrow;
+    long long sum = 0;
+    for (long long r = a; r < b; ++r) {
+        const long long base = r * g.nk[0];
+        sum += (g.cell_start[base + g.nk[0]] - g.cell_start[base] + TW - 1) / TW;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long t = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    long long ex = (w > 0 ? wsum[w - 1] : 0) + inc - sum;
+    for (long long r = a; r < b; ++r) {
+        toff[r] = ex;
+        const long long base = r * g.nk[0];
+        ex += (g.cell_start[base + g.nk[0]] - g.cell_start[base] + TW - 1) / TW;
+    }
+    if (threadIdx.x == 1023) toff[nrow] = ex;
+}
+
 // Cell x of every sorted particle.
 __global__ void k_cell_x(GridDev g, const int *__restrict__ scell, int *__restrict__ sx) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += (long long)gridDim.x * blockDim.x)
@@ -754,11 +794,20 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
     if (bn > (long long)sm_count * 16) bn = (long long)sm_count * 16;
     if (bn < 1) bn = 1;
     ProfScope ps(TAG_SCAN, s);
-    note_launch(need_cell_x ? 3 : 2);
-    if (need_cell_x) k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
-    k_row_tiles_count<<<(unsigned)b, nt, 0, s>>>(g, tcount);
-    cudaError_t e = exclusive_scan_i64(tcount, toff, nrow, scan_tmp, s);
-    if (e != cudaSuccess) return e;
+    if (need_cell_x) {
+        note_launch(1);
+        k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
+    }
+    if (nrow <= ROWS_SMALL_MAX) {
+        note_launch(1);
+        k_row_tiles_scan_small<<<1, 1024, 0, s>>>(g, toff);
+    } else {
+        note_launch(1);
+        k_row_tiles_count<<<(unsigned)b, nt, 0, s>>>(g, tcount);
+        cudaError_t e = exclusive_scan_i64(tcount, toff, nrow, scan_tmp, s);
+        if (e != cudaSuccess) return e;
+    }
+    note_launch(1);
     k_row_tiles_write<<<(unsigned)b, nt, 0, s>>>(g, toff, tiles);
     return cudaGetLastError();
 }

@@ -1,7 +1,8 @@
 // scan_sort.cu -- device-wide exclusive scan and segmented sort used by the
 // counting sort of the binning step and by the CSR assembly.
 //
-// Scan: three launches (tile sums, scan of tile sums, tile scan + offset).
+// Scan: one launch of one block up to SCAN_SMALL_MAX items, else three
+// launches (tile sums, scan of tile sums, tile scan + offset).
 // Sort: every segment is sorted ascending with a bitonic network written so
 // that all comparators put the minimum at the lower index (the first step of
 // each merge compares i with i ^ (k - 1)).  With that form, positions past the
@@ -105,8 +106,52 @@ __global__ void __launch_bounds__(SCAN_NT) k_tile_scan(const int *in, OutT *out,
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (OutT)sums[ntile];
 }
 
+constexpr int SMALL_NT = 1024;
+
+// Exclusive scan across a 1024-thread block (as block_excl_scan_256).
+__device__ long long block_excl_scan_1024(long long v, long long *total) {
+    __shared__ long long wsum[SMALL_NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc = warp_incl_scan(v, lane);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long t = wsum[lane];
+        t = warp_incl_scan(t, lane);
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    long long before = w > 0 ? wsum[w - 1] : 0;
+    *total = wsum[SMALL_NT / 32 - 1];
+    __syncthreads();
+    return before + inc - v;
+}
+
+// One block, one launch: each thread scans a contiguous run of the input.
+template <typename OutT>
+__global__ void __launch_bounds__(SMALL_NT) k_scan_small(const int *__restrict__ in, OutT *__restrict__ out,
+                                                          long long n) {
+    const long long per = (n + SMALL_NT - 1) / SMALL_NT;
+    const long long a = (long long)threadIdx.x * per, b = a + per < n ? a + per : n;
+    long long sum = 0;
+    for (long long i = a; i < b; ++i) sum += in[i];
+    long long total;
+    long long ex = block_excl_scan_1024(sum, &total);
+    for (long long i = a; i < b; ++i) {
+        out[i] = (OutT)ex;
+        ex += in[i];
+    }
+    if (threadIdx.x == 0) out[n] = (OutT)total;
+}
+
 template <typename OutT>
 cudaError_t scan_impl(const int *in, OutT *out, long long n, void *tmp, cudaStream_t s) {
+    if (n <= SCAN_SMALL_MAX) {
+        ProfScope ps(TAG_SCAN, s);
+        note_launch(1);
+        k_scan_small<OutT><<<1, SMALL_NT, 0, s>>>(in, out, n);
+        return cudaGetLastError();
+    }
     long long ntile = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntile == 0) ntile = 1;
     long long *sums = (long long *)tmp;
