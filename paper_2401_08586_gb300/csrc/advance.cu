@@ -16,10 +16,8 @@
 namespace sph {
 namespace {
 
-__device__ __forceinline__ void cell_xyz(int c, const int nk[3], int cc[3]) {
-    cc[0] = c % nk[0];
-    cc[1] = (c / nk[0]) % nk[1];
-    cc[2] = c / (nk[0] * nk[1]);
+__device__ __forceinline__ void cell_xyz(const GridDev &g, int c, int cc[3]) {
+    cell_decompose(g, c, cc[0], cc[1], cc[2]);
 }
 
 // rel64[s] from the positions, each particle in its current cell:
@@ -30,7 +28,7 @@ __global__ void k_rel64_sync(GridDev g, const int *__restrict__ scell, const dou
          s += (long long)gridDim.x * blockDim.x) {
         const int i = g.orig_id[s];
         int cc[3];
-        cell_xyz(scell[s], g.nk, cc);
+        cell_xyz(g, scell[s], cc);
         double a[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < g.dim; ++k) {
             const double sk = __dmul_rn(__dsub_rn(xyz[(long long)i * g.dim + k], g.lo[k]), g.two_over_hc);
@@ -57,7 +55,7 @@ __global__ void k_advance(GridDev g, const int *__restrict__ scell, const double
         if (live) {
             i = g.orig_id[s];
             int cc[3];
-            cell_xyz(scell[s], g.nk, cc);
+            cell_xyz(g, scell[s], cc);
             const double4 r = rel64[s];
             double a[3] = {r.x, r.y, r.z};
             for (int k = 0; k < g.dim; ++k) {

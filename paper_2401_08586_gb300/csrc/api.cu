@@ -54,6 +54,7 @@ static GridDev make_dev(sph_grid_s *g) {
         d.lo[k] = g->lo[k];
     }
     d.ncell = g->ncell;
+    set_divisors(d);
     d.hc = g->hc;
     d.two_over_hc = 2.0 / g->hc;
     // one-FMA binning when every coordinate of the grid lies within 2^17 u of

@@ -469,6 +469,7 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
             d.lo[a] = lo[a];
         }
         d.ncell = nc;
+        set_divisors(d);
         d.hc = hc;
         d.two_over_hc = 2.0 / hc;
         d.xyz = xyz[k];

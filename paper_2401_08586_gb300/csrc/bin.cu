@@ -169,7 +169,7 @@ __global__ void k_convert(int n, int dim, GridDev g, const int *__restrict__ cid
         rank[i] = (int)s;
         const int c = cid_in[i];
         scell[s] = c;
-        if (scell_x != nullptr) scell_x[s] = c % g.nk[0];
+        if (scell_x != nullptr) scell_x[s] = c - (int)fastdiv_div((uint32_t)c, g.div_nx) * g.nk[0];
         if (PREC == SPH_PREC_FP64_CLL) {
             double x[3] = {0.0, 0.0, 0.0};
             for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];

@@ -103,6 +103,11 @@ static unsigned int half2_splat_bits(__half h) {
     return u;
 }
 
+void set_divisors(GridDev &d) {
+    d.div_nx = fastdiv_make((uint32_t)d.nk[0]);
+    d.div_nxy = fastdiv_make((uint32_t)d.nk[0] * (uint32_t)d.nk[1]);
+}
+
 void set_constants(GridDev &d, const sph_params &p, double hc) {
     const double kh = p.kh, h = p.h;
     d.kh2 = kh * kh;

@@ -49,6 +49,8 @@ int validate_params(const sph_params *p, int64_t n, const double *xyz);
 // The precision-tier thresholds and kernel normalisation of a grid with
 // cell size hc (fields kh2 ... w_self64 of GridDev).
 void set_constants(GridDev &d, const sph_params &p, double hc);
+// The launch-invariant divisors of the grid's cell ids (nk filled first).
+void set_divisors(GridDev &d);
 
 // Host launchers of the status-record kernels.
 cudaError_t launch_status_init(DevStatus *st, cudaStream_t s);

@@ -46,12 +46,14 @@ __global__ void k_density(GridDev g, const int *__restrict__ rank, const int *__
         if constexpr (PREC == SPH_PREC_FP16_RCLL) {
             const float4 ri = g.rel32[si];
             const int ci = scell[si];
-            const int cix = ci % g.nk[0], ciy = (ci / g.nk[0]) % g.nk[1], ciz = ci / (g.nk[0] * g.nk[1]);
+            int cix, ciy, ciz;
+            cell_decompose(g, ci, cix, ciy, ciz);
             float acc = g.w_self;
             for (long long q = row_ptr[r]; q < row_ptr[r + 1]; ++q) {
                 const int sj = canonical ? rank[col[q]] : col[q];
                 const int cj = scell[sj];
-                const int cjx = cj % g.nk[0], cjy = (cj / g.nk[0]) % g.nk[1], cjz = cj / (g.nk[0] * g.nk[1]);
+                int cjx, cjy, cjz;
+                cell_decompose(g, cj, cjx, cjy, cjz);
                 const float4 rj = g.rel32[sj];
                 const float d0 = __fsub_rn(__fadd_rn(rj.x, 2.f * (float)(cjx - cix)), ri.x);
                 const float d1 = __fsub_rn(__fadd_rn(rj.y, 2.f * (float)(cjy - ciy)), ri.y);

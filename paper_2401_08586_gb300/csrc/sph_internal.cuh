@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fastdiv.h"
 #include "sph.h"
 
 namespace sph {
@@ -48,6 +49,8 @@ struct GridDev {
     double two_over_hc;  // 2 / h_c: FP64 units -> u
     double neg_lo_t[3];  // -lo * 2 / h_c (binning in one FMA, when fma_bin)
     int fma_bin;         // 1: every coordinate is within 2^17 u of the origin
+    FastDiv div_nx;      // division by nk[0] (cells per row)
+    FastDiv div_nxy;     // division by nk[0] * nk[1] (cells per layer)
     const int *cell_start;
     const uint2 *rel16;   // per sorted particle: half x_rel, y_rel | z_rel, 0
     const float4 *rel32;  // per sorted particle: x_rel, y_rel, z_rel, 0
@@ -68,6 +71,14 @@ struct GridDev {
     double w_self64;
     DevStatus *status;
 };
+
+// Cell coordinates of a linear cell id (c = (cz ny + cy) nx + cx).
+__device__ __forceinline__ void cell_decompose(const GridDev &g, int c, int &cx, int &cy, int &cz) {
+    const int row = (int)fastdiv_div((uint32_t)c, g.div_nx);
+    cz = (int)fastdiv_div((uint32_t)c, g.div_nxy);
+    cx = c - row * g.nk[0];
+    cy = row - cz * g.nk[1];
+}
 
 // Order-preserving map from a finite double to an unsigned 64-bit key.
 __host__ __device__ inline unsigned long long dkey(double x) {

@@ -52,7 +52,8 @@ __global__ void k_precision_study(GridDev g, const int *__restrict__ scell, long
         if (oi < row_begin || oi >= row_end) continue;
         const double *xi = g.xyz + (long long)oi * dim;
         const int ci = scell[s];
-        const int cx = ci % g.nk[0], cy = (ci / g.nk[0]) % g.nk[1], cz = ci / (g.nk[0] * g.nk[1]);
+        int cx, cy, cz;
+        cell_decompose(g, ci, cx, cy, cz);
         const uint2 qi = g.rel16[s];
         const float4 fi = g.rel32[s];
         const __half2 qixy = *reinterpret_cast<const __half2 *>(&qi.x);
