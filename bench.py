@@ -542,7 +542,7 @@ def bench_e2e(sph, ps, dev, stream, args):
 
 
 SERVE_DESC = ("serve: Poisson arrivals at 200 req/s, 70%% 3D / 30%% 2D, N log-uniform in [1e3, 2e6], jittered "
-              "lattices dx = 1/ceil(N^(1/d)), h/dx U[1.2, 1.5], kh = 2h, 64 GB budget, 2 worker streams, seed 5; "
+              "lattices dx = 1/ceil(N^(1/d)), h/dx U[1.2, 1.5], kh = 2h, 64 GB budget, 4 worker streams, seed 5; "
               "%d timed requests after %d warm-up")
 
 
@@ -575,7 +575,7 @@ def bench_serve(sph, dev, count=2000, warm=200, rate=200.0):
     specs = W.c5_request_stream(count=count + warm, rate=rate, materialise=False)
     reqs = [device_request(sp, dev) for _, sp, _ in specs]
     torch.cuda.synchronize()
-    srv = sph.Server(64 << 30, streams=2)
+    srv = sph.Server(64 << 30, streams=4)
     tickets = [None] * len(specs)
     done = {}
     d2h_s = {}

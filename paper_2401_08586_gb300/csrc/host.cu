@@ -147,10 +147,13 @@ __global__ void k_status_init(DevStatus *st) {
     st->ticket = 0;
 }
 
+// Per-query state: the tier counters, the tile ticket and the flags a query
+// raises (capacity, timeout); the binning flags stay.
 __global__ void k_status_reset_counters(DevStatus *st) {
     st->fp32_pairs = 0;
     st->fp64_pairs = 0;
     st->ticket = 0;
+    st->flags &= ~(ST_CAPACITY | ST_TIMEOUT);
 }
 
 cudaError_t launch_status_init(DevStatus *st, cudaStream_t s) {

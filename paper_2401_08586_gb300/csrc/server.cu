@@ -126,22 +126,26 @@ struct ServerWorker {
         SPH_TRY(sph_bin_cells(&r.params, x, r.n, s, &grid));
         SPH_TRY(ensure(q->rp, (size_t)(r.n + 1) * sizeof(int64_t), s));
         if (r.want_density) SPH_TRY(ensure(q->rho, (size_t)(r.n > 0 ? r.n : 1) * sizeof(float), s));
-        // the search writes into the worker's column scratch; the request
-        // keeps an exact-size copy
-        int64_t cap = r.n * nbr_max_for(dim), nnz = 0;
-        if ((int64_t)(bcol.cap / sizeof(int32_t)) > cap) cap = (int64_t)(bcol.cap / sizeof(int32_t));
+        // the search writes straight into the request's column buffer, sized
+        // from the grid's neighbour estimate (particles per cell times the
+        // search sphere's volume in cells, 30 % to spare); a miss re-runs the
+        // search with the exact size
+        sph_grid_info info;
+        SPH_TRY(sph_grid_info_get(grid, &info));
+        const double ppc = info.ncell > 0 ? (double)r.n / (double)info.ncell : 0.0;
+        const double rk = r.params.kh / info.cell_size;
+        const double nbr = dim == 3 ? ppc * 4.18879 * rk * rk * rk : ppc * 3.14159 * rk * rk;
+        int64_t cap = (int64_t)((double)r.n * nbr * 1.3) + 1024, nnz = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
-            SPH_TRY(ensure(bcol, (size_t)(cap > 0 ? cap : 1) * sizeof(int32_t), s));
-            const int rc = sph_nnps_query(grid, P<int64_t>(q->rp), P<int32_t>(bcol), cap, &nnz,
+            SPH_TRY(ensure(q->col, (size_t)cap * sizeof(int32_t), s));
+            const int rc = sph_nnps_query(grid, P<int64_t>(q->rp), P<int32_t>(q->col), cap, &nnz,
                                           r.want_density ? P<float>(q->rho) : nullptr, s);
             if (rc == SPH_OK) break;
             if (rc != SPH_ERR_CAPACITY || attempt == 1) return rc;
+            release(q->col, s);
             cap = nnz;
         }
         q->nnz = nnz;
-        SPH_TRY(ensure(q->col, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t), s));
-        if (nnz > 0)
-            SPH_CUDA(cudaMemcpyAsync(q->col.p, bcol.p, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         SPH_TRY(ensure(q->orig, (size_t)(r.n > 0 ? r.n : 1) * sizeof(int32_t), s));
         if (r.n > 0 && r.params.order == SPH_ORDER_CELL)
             SPH_TRY(sph_grid_export(grid, P<int32_t>(q->orig), nullptr, nullptr, s));

@@ -203,6 +203,14 @@ def test_capacity_error_writes_nothing(sph):
         sph.sph_nnps_query(g.handle, rp, buf, cap)
     assert ei.value.code == sph.SPH_ERR_CAPACITY
     assert torch.all(buf[cap:] == -7)  # nothing at or past the capacity
+    # the same grid, queried again with room: succeeds (the flag was per query)
+    col = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    assert sph.sph_nnps_query(g.handle, rp, col, nnz) == nnz
+    rp_ref, col_ref = oracle.cll(ps.xyz, ps.kh)
+    # cell order -> input order
+    orig = g.orig_id().cpu().numpy()
+    crp, ccol = to_canonical(rp.cpu().numpy(), col.cpu().numpy(), orig)
+    assert np.array_equal(crp, rp_ref) and np.array_equal(ccol, col_ref)
 
 
 def test_unfused_density_matches(sph):
