@@ -315,7 +315,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
     } else if (fused) {
         // single pass, one warp per 32-particle row tile, look-back across tiles
         const long long nrow = (long long)g->nk[1] * g->nk[2];
-        const long long ntiles_max = n / 32 + nrow + 1;
+        const long long ntiles_max = tiles_max(n, g->ncell, nrow);
         SPH_TRY(ensure(g->tcount, nrow * sizeof(int), s));
         SPH_TRY(ensure(g->toff, (nrow + 1) * sizeof(long long), s));
         SPH_TRY(ensure(g->tiles, ntiles_max * sizeof(int4), s));

@@ -156,16 +156,17 @@ __global__ void k_batch_convert(const BinSys *__restrict__ sys, const long long 
     }
 }
 
-// Tiles of 32 per row of cells, over the rows of all systems.
+// Row tiles (row_tile_end) over the rows of all systems.
 __global__ void k_batch_rows_count(const BinSys *__restrict__ sys, const long long *__restrict__ row_first, int nsys,
                                    long long nrow, const int *__restrict__ cell_start, int *__restrict__ tcount) {
     for (long long R = (long long)blockIdx.x * blockDim.x + threadIdx.x; R < nrow;
          R += (long long)gridDim.x * blockDim.x) {
         const int s = find_sys(row_first, nsys, R);
         const BinSys &S = sys[s];
-        const long long c0 = S.cell_base + (R - row_first[s]) * S.nk[0];
-        const int len = cell_start[c0 + S.nk[0]] - cell_start[c0];
-        tcount[R] = (len + 31) / 32;
+        const int *cs = cell_start + S.cell_base + (R - row_first[s]) * S.nk[0];
+        int count = 0, c = 0;
+        for (int p = cs[0]; p < cs[S.nk[0]]; ++count) p = row_tile_end(cs, S.nk[0], p, c);
+        tcount[R] = count;
     }
 }
 
@@ -177,10 +178,14 @@ __global__ void k_batch_rows_write(const BinSys *__restrict__ sys, const long lo
         const int s = find_sys(row_first, nsys, R);
         const BinSys &S = sys[s];
         const long long r = R - row_first[s];
-        const long long c0 = S.cell_base + r * S.nk[0];
-        const int a = cell_start[c0], b = cell_start[c0 + S.nk[0]];
+        const int *cs = cell_start + S.cell_base + r * S.nk[0];
         long long o = toff[R];
-        for (int p = a; p < b; p += 32) tiles[o++] = make_int4(p, min(32, b - p), (int)r, s);
+        int c = 0;
+        for (int p = cs[0]; p < cs[S.nk[0]];) {
+            const int e = row_tile_end(cs, S.nk[0], p, c);
+            tiles[o++] = make_int4(p, e - p, (int)r, s);
+            p = e;
+        }
     }
 }
 
@@ -482,7 +487,7 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     }
     b->h_first[nsys] = off;
     b->h_row_first[nsys] = nrow;
-    const long long ntiles_max = ntot / 32 + nrow + 1;
+    const long long ntiles_max = tiles_max(ntot, ncell, nrow);
     if ((int)ensure(b->cnt, ncell * sizeof(int), s) || ensure(b->cell_start, (ncell + 1) * sizeof(int), s) ||
         ensure(b->cid, nn * sizeof(int), s) || ensure(b->slot, nn * sizeof(int), s) ||
         ensure(b->orig_g, nn * sizeof(int), s) || ensure(b->orig_l, nn * sizeof(int), s) ||

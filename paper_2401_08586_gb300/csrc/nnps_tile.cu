@@ -42,8 +42,8 @@ using namespace nn;
 
 namespace {
 
-constexpr int TW = 32;        // rows per tile
-constexpr int SPANMAX = 4;    // home cells per group along x (keeps |X| < 8)
+constexpr int TW = TILE_ROWS;     // rows per tile
+constexpr int SPANMAX = TILE_SPAN;  // home cells per group along x (keeps |X| < 8)
 constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the culling test
 constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch may ask for
 
@@ -667,38 +667,48 @@ __global__ void __launch_bounds__(32, 16) k_nnps_tile(GridDev g0, const GridDev 
     }
 }
 
-// Tiles per x-row of cells: ceil(particles / 32).
-__global__ void k_row_tiles_count(GridDev g, int *__restrict__ tcount) {
-    const long long nrow = (long long)g.nk[1] * g.nk[2];
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrow; r += (long long)gridDim.x * blockDim.x) {
-        const long long base = r * g.nk[0];
-        const int len = g.cell_start[base + g.nk[0]] - g.cell_start[base];
-        tcount[r] = (len + TW - 1) / TW;
-    }
+// Tiles of one row of cells: span-limited (row_tile_end) or plain runs of
+// TW particles (span_limited false: the no-allocation path, whose fixed
+// scratch is sized for n / TW + nrow tiles).
+__device__ __forceinline__ int row_tile_count(const int *cs, int nx, bool span_limited) {
+    if (!span_limited) return (cs[nx] - cs[0] + TW - 1) / TW;
+    int count = 0, c = 0;
+    for (int p = cs[0]; p < cs[nx]; ++count) p = row_tile_end(cs, nx, p, c);
+    return count;
 }
 
-__global__ void k_row_tiles_write(GridDev g, const long long *__restrict__ toff, int4 *__restrict__ tiles) {
+__global__ void k_row_tiles_count(GridDev g, int *__restrict__ tcount, bool span_limited) {
+    const long long nrow = (long long)g.nk[1] * g.nk[2];
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrow; r += (long long)gridDim.x * blockDim.x)
+        tcount[r] = row_tile_count(g.cell_start + r * g.nk[0], g.nk[0], span_limited);
+}
+
+__global__ void k_row_tiles_write(GridDev g, const long long *__restrict__ toff, int4 *__restrict__ tiles,
+                                  bool span_limited) {
     const long long nrow = (long long)g.nk[1] * g.nk[2];
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrow; r += (long long)gridDim.x * blockDim.x) {
-        const long long base = r * g.nk[0];
-        const int a = g.cell_start[base], b = g.cell_start[base + g.nk[0]];
+        const int *cs = g.cell_start + r * g.nk[0];
+        const int nx = g.nk[0];
         long long o = toff[r];
-        for (int p = a; p < b; p += TW) tiles[o++] = make_int4(p, min(TW, b - p), (int)r, 0);
+        int c = 0;
+        for (int p = cs[0]; p < cs[nx];) {
+            const int e = span_limited ? row_tile_end(cs, nx, p, c) : min(p + TW, cs[nx]);
+            tiles[o++] = make_int4(p, e - p, (int)r, 0);
+            p = e;
+        }
     }
 }
 
-// Grids of nrow <= ROWS_SMALL_MAX rows: tiles per row and their exclusive
+// Grids of at most ROWS_SMALL_MAX cells: tiles per row and their exclusive
 // scan in one single-block launch (each thread a contiguous run of rows).
-__global__ void __launch_bounds__(1024) k_row_tiles_scan_small(GridDev g, long long *__restrict__ toff) {
+__global__ void __launch_bounds__(1024) k_row_tiles_scan_small(GridDev g, long long *__restrict__ toff,
+                                                               bool span_limited) {
     __shared__ long long wsum[32];
     const long long nrow = (long long)g.nk[1] * g.nk[2];
     const long long per = (nrow + 1023) / 1024;
     const long long a = (long long)threadIdx.x * per, b = a + per < nrow ? a + per : nrow;
     long long sum = 0;
-    for (long long r = a; r < b; ++r) {
-        const long long base = r * g.nk[0];
-        sum += (g.cell_start[base + g.nk[0]] - g.cell_start[base] + TW - 1) / TW;
-    }
+    for (long long r = a; r < b; ++r) sum += row_tile_count(g.cell_start + r * g.nk[0], g.nk[0], span_limited);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     long long inc = sum;
 #pragma unroll
@@ -721,8 +731,7 @@ __global__ void __launch_bounds__(1024) k_row_tiles_scan_small(GridDev g, long l
     long long ex = (w > 0 ? wsum[w - 1] : 0) + inc - sum;
     for (long long r = a; r < b; ++r) {
         toff[r] = ex;
-        const long long base = r * g.nk[0];
-        ex += (g.cell_start[base + g.nk[0]] - g.cell_start[base] + TW - 1) / TW;
+        ex += row_tile_count(g.cell_start + r * g.nk[0], g.nk[0], span_limited);
     }
     if (threadIdx.x == 1023) toff[nrow] = ex;
 }
@@ -785,6 +794,8 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
 // tiles: int4[ntiles_max] with ntiles_max = n / 32 + nrow.
 cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
                          long long *toff, void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s) {
+    // the no-allocation path (need_cell_x) keeps plain runs of TW particles
+    const bool span_limited = !need_cell_x;
     const long long nrow = (long long)g.nk[1] * g.nk[2];
     const int nt = 256;
     long long b = (nrow + nt - 1) / nt;
@@ -798,17 +809,17 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
         note_launch(1);
         k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
     }
-    if (nrow <= ROWS_SMALL_MAX) {
+    if (g.ncell <= ROWS_SMALL_MAX) {
         note_launch(1);
-        k_row_tiles_scan_small<<<1, 1024, 0, s>>>(g, toff);
+        k_row_tiles_scan_small<<<1, 1024, 0, s>>>(g, toff, span_limited);
     } else {
         note_launch(1);
-        k_row_tiles_count<<<(unsigned)b, nt, 0, s>>>(g, tcount);
+        k_row_tiles_count<<<(unsigned)b, nt, 0, s>>>(g, tcount, span_limited);
         cudaError_t e = exclusive_scan_i64(tcount, toff, nrow, scan_tmp, s);
         if (e != cudaSuccess) return e;
     }
     note_launch(1);
-    k_row_tiles_write<<<(unsigned)b, nt, 0, s>>>(g, toff, tiles);
+    k_row_tiles_write<<<(unsigned)b, nt, 0, s>>>(g, toff, tiles, span_limited);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,25 @@ __device__ __forceinline__ void round_rel(const double a[3], uint2 &q16, float4 
     f32 = make_float4(f0, f1, f2, 0.f);
 }
 
+// Row tiles of the single-pass search: runs of at most TILE_ROWS
+// consecutive particles of one row of cells that lie within TILE_SPAN
+// consecutive cells, cut greedily from the row's start.  cs: the row's nx + 1
+// cell starts; p: the first particle of the tile (p < cs[nx]); c: a cell at
+// or before the one holding p (advanced in place).  Returns the end of the
+// tile.  A row of len particles has at most len / TILE_ROWS + nx / TILE_SPAN
+// + 1 tiles.
+constexpr int TILE_ROWS = 32;
+constexpr int TILE_SPAN = 4;
+__host__ __device__ __forceinline__ int row_tile_end(const int *cs, int nx, int p, int &c) {
+    while (cs[c + 1] <= p) ++c;
+    const int ce = c + TILE_SPAN < nx ? c + TILE_SPAN : nx;
+    const int e = p + TILE_ROWS;
+    return e < cs[ce] ? e : cs[ce];
+}
+__host__ __device__ __forceinline__ long long tiles_max(long long n, long long ncell, long long nrow) {
+    return n / TILE_ROWS + ncell / TILE_SPAN + nrow + 1;
+}
+
 // What another translation unit of the library may see of a grid
 // (filled by grid_view in api.cu).
 struct GridView {
@@ -165,7 +184,7 @@ void reset_counters_async(DevStatus *st, cudaStream_t s);
 // scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(long long n);
 constexpr long long SCAN_SMALL_MAX = 1LL << 14;  // scans this short run in one single-block launch
-constexpr long long ROWS_SMALL_MAX = 1LL << 17;  // tile lists of this many rows: one single-block scan
+constexpr long long ROWS_SMALL_MAX = 1LL << 17;  // tile lists of grids of this many cells: one single-block scan
 cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t s);
 cudaError_t exclusive_scan_i64(const int *in, long long *out, long long n, void *tmp,
                                cudaStream_t s);
