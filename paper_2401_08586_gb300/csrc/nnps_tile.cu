@@ -31,6 +31,8 @@
 // then emit straight to their rows after the look-back).
 #include <stddef.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "launch.cuh"
@@ -669,7 +671,7 @@ __global__ void __launch_bounds__(32, 16) k_nnps_tile(GridDev g0, const GridDev 
 
 // Tiles of one row of cells: span-limited (row_tile_end) or plain runs of
 // TW particles (span_limited false: the no-allocation path, whose fixed
-// scratch is sized for n / TW + nrow tiles).
+// scratch is sized for n / TW + nrow tiles).  cs: the row's nx + 1 starts.
 __device__ __forceinline__ int row_tile_count(const int *cs, int nx, bool span_limited) {
     if (!span_limited) return (cs[nx] - cs[0] + TW - 1) / TW;
     int count = 0, c = 0;
@@ -677,63 +679,46 @@ __device__ __forceinline__ int row_tile_count(const int *cs, int nx, bool span_l
     return count;
 }
 
-__global__ void k_row_tiles_count(GridDev g, int *__restrict__ tcount, bool span_limited) {
-    const long long nrow = (long long)g.nk[1] * g.nk[2];
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrow; r += (long long)gridDim.x * blockDim.x)
-        tcount[r] = row_tile_count(g.cell_start + r * g.nk[0], g.nk[0], span_limited);
-}
+constexpr int ROWTILE_NT = 256;
+constexpr int ROWTILE_SMEM_INTS = 8192;  // cell starts staged per chunk of rows (32 KB)
 
-__global__ void k_row_tiles_write(GridDev g, const long long *__restrict__ toff, int4 *__restrict__ tiles,
-                                  bool span_limited) {
+// Row tiles, counted (tcount != nullptr) or written (tiles at toff).  Each
+// block takes chunks of whole rows whose cell starts fit in shared memory,
+// copies them with coalesced loads, and one thread per row walks its row
+// there; rows longer than the buffer are walked from global memory.
+__global__ void __launch_bounds__(ROWTILE_NT) k_row_tiles(GridDev g, int *__restrict__ tcount,
+                                                          const long long *__restrict__ toff,
+                                                          int4 *__restrict__ tiles, bool span_limited) {
+    __shared__ int cs_s[ROWTILE_SMEM_INTS];
     const long long nrow = (long long)g.nk[1] * g.nk[2];
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrow; r += (long long)gridDim.x * blockDim.x) {
-        const int *cs = g.cell_start + r * g.nk[0];
-        const int nx = g.nk[0];
-        long long o = toff[r];
-        int c = 0;
-        for (int p = cs[0]; p < cs[nx];) {
-            const int e = span_limited ? row_tile_end(cs, nx, p, c) : min(p + TW, cs[nx]);
-            tiles[o++] = make_int4(p, e - p, (int)r, 0);
-            p = e;
+    const int nx = g.nk[0];
+    const bool staged = nx + 1 <= ROWTILE_SMEM_INTS;
+    const int rpc = staged ? min(ROWTILE_NT, (ROWTILE_SMEM_INTS - 1) / nx) : ROWTILE_NT;  // rows per chunk
+    for (long long r0 = (long long)blockIdx.x * rpc; r0 < nrow; r0 += (long long)gridDim.x * rpc) {
+        const int rows = (int)min((long long)rpc, nrow - r0);
+        const int *cs = g.cell_start + r0 * nx;
+        if (staged) {
+            __syncthreads();
+            for (int k = threadIdx.x; k <= rows * nx; k += ROWTILE_NT) cs_s[k] = cs[k];
+            __syncthreads();
+            cs = cs_s;
+        }
+        if (threadIdx.x < rows) {
+            const long long r = r0 + threadIdx.x;
+            const int *row = cs + (long long)threadIdx.x * nx;
+            if (tcount != nullptr) {
+                tcount[r] = row_tile_count(row, nx, span_limited);
+            } else {
+                long long o = toff[r];
+                int c = 0;
+                for (int p = row[0]; p < row[nx];) {
+                    const int e = span_limited ? row_tile_end(row, nx, p, c) : min(p + TW, row[nx]);
+                    tiles[o++] = make_int4(p, e - p, (int)r, 0);
+                    p = e;
+                }
+            }
         }
     }
-}
-
-// Grids of at most ROWS_SMALL_MAX cells: tiles per row and their exclusive
-// scan in one single-block launch (each thread a contiguous run of rows).
-__global__ void __launch_bounds__(1024) k_row_tiles_scan_small(GridDev g, long long *__restrict__ toff,
-                                                               bool span_limited) {
-    __shared__ long long wsum[32];
-    const long long nrow = (long long)g.nk[1] * g.nk[2];
-    const long long per = (nrow + 1023) / 1024;
-    const long long a = (long long)threadIdx.x * per, b = a + per < nrow ? a + per : nrow;
-    long long sum = 0;
-    for (long long r = a; r < b; ++r) sum += row_tile_count(g.cell_start + r * g.nk[0], g.nk[0], span_limited);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    long long inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        long long t = wsum[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        wsum[lane] = t;
-    }
-    __syncthreads();
-    long long ex = (w > 0 ? wsum[w - 1] : 0) + inc - sum;
-    for (long long r = a; r < b; ++r) {
-        toff[r] = ex;
-        ex += row_tile_count(g.cell_start + r * g.nk[0], g.nk[0], span_limited);
-    }
-    if (threadIdx.x == 1023) toff[nrow] = ex;
 }
 
 // Cell x of every sorted particle.
@@ -798,9 +783,6 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
     const bool span_limited = !need_cell_x;
     const long long nrow = (long long)g.nk[1] * g.nk[2];
     const int nt = 256;
-    long long b = (nrow + nt - 1) / nt;
-    if (b > (long long)sm_count * 8) b = (long long)sm_count * 8;
-    if (b < 1) b = 1;
     long long bn = (g.n + nt - 1) / nt;
     if (bn > (long long)sm_count * 16) bn = (long long)sm_count * 16;
     if (bn < 1) bn = 1;
@@ -809,17 +791,17 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
         note_launch(1);
         k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
     }
-    if (g.ncell <= ROWS_SMALL_MAX) {
-        note_launch(1);
-        k_row_tiles_scan_small<<<1, 1024, 0, s>>>(g, toff, span_limited);
-    } else {
-        note_launch(1);
-        k_row_tiles_count<<<(unsigned)b, nt, 0, s>>>(g, tcount, span_limited);
-        cudaError_t e = exclusive_scan_i64(tcount, toff, nrow, scan_tmp, s);
-        if (e != cudaSuccess) return e;
-    }
-    note_launch(1);
-    k_row_tiles_write<<<(unsigned)b, nt, 0, s>>>(g, toff, tiles, span_limited);
+    const int nx = g.nk[0];
+    const long long rpc = nx + 1 <= ROWTILE_SMEM_INTS ? std::min<long long>(ROWTILE_NT, (ROWTILE_SMEM_INTS - 1) / nx)
+                                                      : ROWTILE_NT;
+    long long rb = (nrow + rpc - 1) / rpc;
+    if (rb > (long long)sm_count * 8) rb = (long long)sm_count * 8;
+    if (rb < 1) rb = 1;
+    note_launch(2);
+    k_row_tiles<<<(unsigned)rb, ROWTILE_NT, 0, s>>>(g, tcount, nullptr, nullptr, span_limited);
+    cudaError_t e = exclusive_scan_i64(tcount, toff, nrow, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_row_tiles<<<(unsigned)rb, ROWTILE_NT, 0, s>>>(g, nullptr, toff, tiles, span_limited);
     return cudaGetLastError();
 }
 

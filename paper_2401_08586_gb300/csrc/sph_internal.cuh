@@ -184,7 +184,6 @@ void reset_counters_async(DevStatus *st, cudaStream_t s);
 // scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(long long n);
 constexpr long long SCAN_SMALL_MAX = 1LL << 14;  // scans this short run in one single-block launch
-constexpr long long ROWS_SMALL_MAX = 1LL << 17;  // tile lists of grids of this many cells: one single-block scan
 cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t s);
 cudaError_t exclusive_scan_i64(const int *in, long long *out, long long n, void *tmp,
                                cudaStream_t s);
