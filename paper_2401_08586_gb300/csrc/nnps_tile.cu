@@ -679,7 +679,7 @@ __device__ __forceinline__ int row_tile_count(const int *cs, int nx, bool span_l
     return count;
 }
 
-constexpr int ROWTILE_NT = 256;
+constexpr int ROWTILE_NT = 64;            // threads per block = most rows per chunk
 constexpr int ROWTILE_SMEM_INTS = 8192;  // cell starts staged per chunk of rows (32 KB)
 
 // Row tiles, counted (tcount != nullptr) or written (tiles at toff).  Each
@@ -795,7 +795,7 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
     const long long rpc = nx + 1 <= ROWTILE_SMEM_INTS ? std::min<long long>(ROWTILE_NT, (ROWTILE_SMEM_INTS - 1) / nx)
                                                       : ROWTILE_NT;
     long long rb = (nrow + rpc - 1) / rpc;
-    if (rb > (long long)sm_count * 8) rb = (long long)sm_count * 8;
+    if (rb > (long long)sm_count * 16) rb = (long long)sm_count * 16;
     if (rb < 1) rb = 1;
     note_launch(2);
     k_row_tiles<<<(unsigned)rb, ROWTILE_NT, 0, s>>>(g, tcount, nullptr, nullptr, span_limited);
