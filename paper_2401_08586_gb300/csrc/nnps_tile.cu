@@ -50,18 +50,22 @@ constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the cu
 constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch may ask for
 
 // Shared-memory shape of the tile search: kept candidates per pass (the
-// bitmask length) and per staging window.  The sparse shape needs 12.6 KB per
-// warp, so 16 one-warp CTAs fit an SM (the register limit); the dense shape
-// (15.6 KB, 13 per SM) keeps more candidates per pass for denser particle sets.
-template <int CMAX_, int WIN_>
+// bitmask length), per staging window, and warps per CTA.  Each warp works
+// alone on its own tiles in its own shared-memory area; two warps per CTA
+// share the SM's per-CTA reservation, so both shapes (13.1 and 13.7 KB per
+// warp) fit 16 warps per SM, the register limit.  The dense shape keeps more
+// candidates per pass for denser particle sets (fewer tiles run twice).
+template <int CMAX_, int WIN_, int WPB_>
 struct TileCfg {
     static constexpr int CMAX = CMAX_;
     static constexpr int WIN = WIN_;
+    static constexpr int WPB = WPB_;
     static constexpr int NWORD = CMAX_ / 32;
     static_assert(CMAX_ % 32 == 0 && WIN_ % 32 == 0 && WIN_ <= CMAX_, "tile shape");
+    static_assert(16 % WPB_ == 0, "warps per CTA");
 };
-using TileSparse = TileCfg<768, 224>;
-using TileDense = TileCfg<1024, 256>;
+using TileSparse = TileCfg<768, 256, 2>;
+using TileDense = TileCfg<832, 256, 2>;
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
@@ -558,15 +562,15 @@ __device__ __forceinline__ void emit_bits(const TileSmem<C> &S, int lane, int nw
 // system's GridDev from gsys, g0 carries the shared status record and the
 // length of the concatenated sorted arrays.  Otherwise g0 is the grid.
 template <int DIM, bool BATCH, class C>
-__global__ void __launch_bounds__(32, 16) k_nnps_tile(GridDev g0, const GridDev *__restrict__ gsys,
-                                                 const int4 *__restrict__ tiles,
-                                                 const long long *__restrict__ ntiles_dev,
-                                                 long long *__restrict__ row_ptr, int *__restrict__ col,
-                                                 long long cap, float *__restrict__ rho,
-                                                 unsigned long long *__restrict__ tstate, int stg_slots) {
+__global__ void __launch_bounds__(32 * C::WPB, 16 / C::WPB)
+    k_nnps_tile(GridDev g0, const GridDev *__restrict__ gsys, const int4 *__restrict__ tiles,
+                const long long *__restrict__ ntiles_dev, long long *__restrict__ row_ptr, int *__restrict__ col,
+                long long cap, float *__restrict__ rho, unsigned long long *__restrict__ tstate, int stg_slots,
+                int warp_bytes) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    TileSmem<C> &S = *reinterpret_cast<TileSmem<C> *>(smraw);
-    const int lane = threadIdx.x;
+    // this warp's area: TileSmem, then its share of the extra staging
+    TileSmem<C> &S = *reinterpret_cast<TileSmem<C> *>(smraw + (threadIdx.x >> 5) * warp_bytes);
+    const int lane = threadIdx.x & 31;
     const bool want_rho = rho != nullptr;
     const long long ntiles = *ntiles_dev;
     unsigned int n32 = 0, n64 = 0;
@@ -736,13 +740,20 @@ constexpr bool staging_contiguous() {
            sizeof(TileSmem<C>) == offsetof(TileSmem<C>, f32) + sizeof(TileSmem<C>::f32);
 }
 static_assert(staging_contiguous<TileSparse>() && staging_contiguous<TileDense>(), "staging layout");
+// the largest launch (every warp with the most extra staging) stays within
+// the 227 KB a CTA may opt into
+template <class C>
+constexpr bool fits_cta() { return (sizeof(TileSmem<C>) + TILE_MAX_EXTRA_SMEM) * C::WPB <= 232448; }
+static_assert(fits_cta<TileSparse>() && fits_cta<TileDense>(), "shared memory per CTA");
 
 template <class C>
 cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                          long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
                          unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s) {
     using SM = TileSmem<C>;
-    const size_t sb = sizeof(SM) + (size_t)extra_smem;
+    extra_smem = (extra_smem + 15) & ~15;  // keeps every warp's area 16-byte aligned
+    const size_t warp_bytes = sizeof(SM) + (size_t)extra_smem;
+    const size_t sb = warp_bytes * C::WPB;
     const bool batch = gsys != nullptr;
     const int ki = (g.dim == 2 ? 0 : 2) + (batch ? 1 : 0);
     auto kern = ki == 0 ? k_nnps_tile<2, false, C> : ki == 1 ? k_nnps_tile<2, true, C>
@@ -754,14 +765,14 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
     static cudaError_t once_err[4];
     std::call_once(once[ki], [&] {
         once_err[ki] = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(sizeof(SM) + TILE_MAX_EXTRA_SMEM));
+                                            (int)((sizeof(SM) + TILE_MAX_EXTRA_SMEM) * C::WPB));
     });
     if (once_err[ki] != cudaSuccess) return once_err[ki];
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, sb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * C::WPB, sb);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)sm_count * per_sm;
-    if (blocks > ntiles_max) blocks = ntiles_max;
+    if (blocks > (ntiles_max + C::WPB - 1) / C::WPB) blocks = (ntiles_max + C::WPB - 1) / C::WPB;
     if (blocks < 1) blocks = 1;
     cudaError_t e =
         cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
@@ -769,7 +780,8 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
     const int stg_slots = (int)((SM::staging_bytes() + (size_t)extra_smem) / 2);
     ProfScope ps(TAG_FUSED, s);
     note_launch(1);
-    kern<<<(unsigned)blocks, 32, sb, s>>>(g, gsys, tiles, ntiles_dev, row_ptr, col, cap, rho, tstate, stg_slots);
+    kern<<<(unsigned)blocks, 32 * C::WPB, sb, s>>>(g, gsys, tiles, ntiles_dev, row_ptr, col, cap, rho, tstate,
+                                                    stg_slots, (int)warp_bytes);
     return cudaGetLastError();
 }
 
