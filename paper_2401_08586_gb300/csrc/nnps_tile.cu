@@ -76,8 +76,11 @@ template <class C>
 struct TileSmem {
     unsigned int S[TW][C::NWORD + 1];
     int jall[C::CMAX];  // kept candidates: sorted index
-    int selfpos[TW];    // kept slot of each lane's own particle (-1: not in this fill)
-    int rstart[9], rlen[9], rcum[10], pad[4];  // candidate rows: start, length, flat prefix
+    short selfpos[TW];  // kept slot of each lane's own particle (-1: not in this fill)
+    // candidate rows r: sorted index minus flat index of the row's candidates,
+    // code bits (dy + 1) << 3 | (dz + 1) << 5, frame shifts 2 dy and 2 dz (float bits)
+    int4 rt[9];
+    int rcum[10], pad[2];  // flat index of row r's first candidate; [nrows] = total
     // code, pw and f32 come last and are contiguous with any extra dynamic
     // shared memory of the launch: after the last window they hold the tile's
     // staged output (16-bit kept-candidate slots), stg_slots of them
@@ -200,15 +203,12 @@ __device__ __forceinline__ void group_rows(TileSmem<C> &S, const GridDev &g, int
             v = g.cell_start[((long long)zz * ny + yy) * nx + (e ? G.xhi + 1 : G.xlo)];
     }
     const int vend = __shfl_down_sync(0xffffffffu, v, 1);
-    int len = 0;
-    if (lane < 2 * NROWS && e == 0) {
-        S.rstart[r] = v >= 0 ? v : 0;
-        len = v >= 0 ? vend - v : 0;
-    }
-    // rows to lanes 0 .. NROWS-1
-    len = __shfl_sync(0xffffffffu, len, 2 * (lane < NROWS ? lane : 0));
+    const int mylen = (e == 0 && v >= 0) ? vend - v : 0;
+    // rows to lanes 0 .. NROWS-1: start and length
+    const int src = 2 * (lane < NROWS ? lane : 0);
+    const int st = __shfl_sync(0xffffffffu, v, src);
+    int len = __shfl_sync(0xffffffffu, mylen, src);
     if (lane >= NROWS) len = 0;
-    if (lane < NROWS) S.rlen[lane] = len;
     // flat index of the candidates: rcum[r] = candidates in rows before r
     int inc = len;
 #pragma unroll
@@ -216,7 +216,13 @@ __device__ __forceinline__ void group_rows(TileSmem<C> &S, const GridDev &g, int
         const int up = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += up;
     }
-    if (lane < 9) S.rcum[lane + 1] = inc;
+    if (lane < NROWS) {
+        const int dy = DIM == 3 ? (lane % 3) - 1 : lane - 1;
+        const int dz = DIM == 3 ? (lane / 3) - 1 : 0;
+        S.rt[lane] = make_int4((st >= 0 ? st : 0) - (inc - len), ((dy + 1) << 3) | ((dz + 1) << 5),
+                               __float_as_int(2.f * (float)dy), __float_as_int(2.f * (float)dz));
+        S.rcum[lane + 1] = inc;
+    }
     if (lane == 0) S.rcum[0] = 0;
     __syncwarp();
 }
@@ -235,10 +241,10 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
     const int lane = threadIdx.x & 31;
     S.selfpos[lane] = -1;
     __syncwarp();
-    int rc[NROWS + 1];
+    int rc[NROWS];
 #pragma unroll
-    for (int r = 0; r <= NROWS; ++r) rc[r] = S.rcum[r];
-    const int total = rc[NROWS];
+    for (int r = 0; r < NROWS; ++r) rc[r] = S.rcum[r + 1];
+    const int total = rc[NROWS - 1];
     int kept = 0;
     while (cur < total && kept + 32 <= C::CMAX) {
         const int nu = kept + 32 * U <= C::CMAX ? U : 1;  // warp-uniform
@@ -249,30 +255,24 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
         for (int u = 0; u < U; ++u) {
             const int k = cur + 32 * u + lane;
             valid[u] = u < nu && k < total;
-            int r = 0, base = 0;  // row of flat index k and the row's first flat index
+            int r = 0;  // row of flat index k: rows before it end at or below k
 #pragma unroll
-            for (int t = 1; t < NROWS; ++t) {
-                const bool past = k >= rc[t];
-                r += past ? 1 : 0;
-                base = past ? rc[t] : base;
-            }
+            for (int t = 0; t < NROWS - 1; ++t) r += k >= rc[t] ? 1 : 0;
             rr[u] = r;
-            jk[u] = S.rstart[r] + (k - base);
+            jk[u] = k + S.rt[r].x;
             q[u] = valid[u] ? g.rel16[jk[u]] : make_uint2(0u, 0u);
             cx[u] = valid[u] ? g.scell_x[jk[u]] : G.xm;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (u >= nu) break;
-            const int r = rr[u];
-            const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
-            const int dz = DIM == 3 ? (r / 3) - 1 : 0;
+            const int4 rt = S.rt[rr[u]];
             const int ox = cx[u] - G.xm;  // frame cell offset in x, |ox| <= 3
             bool keep = false;
             if (valid[u]) {
                 const float2 xy = __half22float2(as_h2(q[u].x));
-                const float x = xy.x + 2.f * (float)ox, y = xy.y + 2.f * (float)dy;
-                const float z = __low2float(as_h2(q[u].y)) + 2.f * (float)dz;
+                const float x = xy.x + 2.f * (float)ox, y = xy.y + __int_as_float(rt.z);
+                const float z = __low2float(as_h2(q[u].y)) + __int_as_float(rt.w);
                 const float ex = fmaxf(fmaxf(G.lo[0] - x, x - G.hi[0]), 0.f);
                 const float ey = fmaxf(fmaxf(G.lo[1] - y, y - G.hi[1]), 0.f);
                 const float ez = fmaxf(fmaxf(G.lo[2] - z, z - G.hi[2]), 0.f);
@@ -282,9 +282,9 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
             if (keep) {
                 const int pos = kept + __popc(m & ((1u << lane) - 1u));
                 S.jall[pos] = jk[u];
-                S.code[pos] = (unsigned char)((ox + 3) | ((dy + 1) << 3) | ((dz + 1) << 5));
+                S.code[pos] = (unsigned char)((ox + 3) | rt.y);
                 // the tile's own particles are the contiguous range [p0, p0 + nhome)
-                if (jk[u] >= p0 && jk[u] < p0 + nhome) S.selfpos[jk[u] - p0] = pos;
+                if (jk[u] >= p0 && jk[u] < p0 + nhome) S.selfpos[jk[u] - p0] = (short)pos;
             }
             kept += __popc(m);
         }
