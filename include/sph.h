@@ -250,9 +250,10 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *     result); more staging lowers the number of resident warps. */
 #define SPH_OPT_STAGING 2
 /*   SPH_OPT_TILE_SHAPE: shared-memory shape of the tile search: -1 (default)
- *     chosen from the neighbours per particle, 0 sparse (up to 768 kept
- *     candidates per pass of a tile), 1 dense (832); both 16 resident warps
- *     per SM.  Same results either way. */
+ *     chosen from the neighbours per particle, 0 sparse (up to 672 kept
+ *     candidates per pass of a tile, 20 resident warps per SM, output staged
+ *     for tiles of up to ~80 neighbours per row), 1 dense (832 kept
+ *     candidates, 16 warps).  Same results either way. */
 #define SPH_OPT_TILE_SHAPE 3
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 

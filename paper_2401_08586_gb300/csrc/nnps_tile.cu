@@ -50,22 +50,26 @@ constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the cu
 constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch may ask for
 
 // Shared-memory shape of the tile search: kept candidates per pass (the
-// bitmask length), per staging window, and warps per CTA.  Each warp works
-// alone on its own tiles in its own shared-memory area; two warps per CTA
-// share the SM's per-CTA reservation, so both shapes (13.1 and 13.7 KB per
-// warp) fit 16 warps per SM, the register limit.  The dense shape keeps more
-// candidates per pass for denser particle sets (fewer tiles run twice).
-template <int CMAX_, int WIN_, int WPB_>
+// bitmask length), per staging window, warps per CTA and the resident warps
+// per SM it is built for (the register budget: 96 per thread at 20 warps,
+// 128 at 16).  Each warp works alone on its own tiles in its own
+// shared-memory area; two warps per CTA share the SM's per-CTA reservation.
+// Sparse: 10.8 KB per warp, 20 warps per SM; its output area (code, pw and
+// f32 after the last window) holds 2,640 entries, a tile of 32 rows of up to
+// ~80 neighbours.  Dense: 13.7 KB, 16 warps, 832 kept candidates and 3,488
+// output entries for denser particle sets.
+template <int CMAX_, int WIN_, int WPB_, int WSM_>
 struct TileCfg {
     static constexpr int CMAX = CMAX_;
     static constexpr int WIN = WIN_;
     static constexpr int WPB = WPB_;
+    static constexpr int WSM = WSM_;
     static constexpr int NWORD = CMAX_ / 32;
     static_assert(CMAX_ % 32 == 0 && WIN_ % 32 == 0 && WIN_ <= CMAX_, "tile shape");
-    static_assert(16 % WPB_ == 0, "warps per CTA");
+    static_assert(WSM_ % WPB_ == 0, "warps per CTA");
 };
-using TileSparse = TileCfg<768, 256, 2>;
-using TileDense = TileCfg<832, 256, 2>;
+using TileSparse = TileCfg<672, 192, 2, 20>;
+using TileDense = TileCfg<832, 256, 2, 16>;
 
 constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
@@ -562,7 +566,7 @@ __device__ __forceinline__ void emit_bits(const TileSmem<C> &S, int lane, int nw
 // system's GridDev from gsys, g0 carries the shared status record and the
 // length of the concatenated sorted arrays.  Otherwise g0 is the grid.
 template <int DIM, bool BATCH, class C>
-__global__ void __launch_bounds__(32 * C::WPB, 16 / C::WPB)
+__global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
     k_nnps_tile(GridDev g0, const GridDev *__restrict__ gsys, const int4 *__restrict__ tiles,
                 const long long *__restrict__ ntiles_dev, long long *__restrict__ row_ptr, int *__restrict__ col,
                 long long cap, float *__restrict__ rho, unsigned long long *__restrict__ tstate, int stg_slots,
@@ -835,14 +839,17 @@ cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *
 }
 
 // Shape and staging for a grid whose rows hold about `nbr` neighbours on
-// average.  Up to 90 neighbours the candidates kept per group stay well
-// under the sparse shape's 768; beyond, the dense shape.  Extra staging only
-// when a tile of 32 such rows (with 15% to spare) needs more than 1.5 times
-// the built-in area: measured on 1M and 8M particle sets, the occupancy it
-// costs outweighs the coalesced output for the tiles just above the area.
+// average.  The sparse shape (more resident warps) while a tile of 32 such
+// rows, with 5% to spare, fits its output area: measured on lattices of 77
+// to 89 neighbours per particle, tiles beyond it write their rows directly
+// and the dense shape is faster once most do.  Extra staging only when a
+// tile of 32 rows (with 15% to spare) needs more than 1.5 times the built-in
+// area: measured on 1M and 8M particle sets, the occupancy it costs
+// outweighs the coalesced output for the tiles just above the area.
 TileLaunch tile_choose(double nbr, int shape) {
     TileLaunch v;
-    v.shape = shape >= 0 ? shape : (nbr < 90.0 ? TILE_SPARSE : TILE_DENSE);
+    const double sparse_slots = (double)TileSmem<TileSparse>::staging_bytes() / 2.0;
+    v.shape = shape >= 0 ? shape : (32.0 * nbr * 1.05 <= sparse_slots ? TILE_SPARSE : TILE_DENSE);
     const double have = (double)(v.shape == TILE_DENSE ? TileSmem<TileDense>::staging_bytes()
                                                         : TileSmem<TileSparse>::staging_bytes());
     const double want = 32.0 * nbr * 1.15 * 2.0;  // bytes of 16-bit slots

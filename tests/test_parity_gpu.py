@@ -275,12 +275,16 @@ def test_nonfinite_in_tail_rejected(sph, where):
 
 
 @pytest.mark.parametrize("shape,staging", [(0, 0), (1, 0), (0, 4096), (1, 2048)])
-@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "dambreak_small", "random3d_dense"])
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "dambreak_small", "random3d_dense", "lattice3d_wide"])
 def test_tile_shapes_and_staging(sph, case, shape, staging):
     """Both shared-memory shapes of the tile search, with and without extra
-    staging, give the oracle's lists and densities."""
+    staging, give the oracle's lists and densities.  lattice3d_wide (kh =
+    3.2 dx, ~130 neighbours per particle) gives tiles whose output is larger
+    than the staging area, so it is staged and copied in several chunks."""
     if case == "random3d_dense":
         xyz, h = W.random_uniform(20000, 3, 21), 0.05  # ~110 neighbours per particle
+    elif case == "lattice3d_wide":
+        xyz, h = W.c2_3d_1m(side=24).xyz, 0.016
     else:
         xyz, h = CASES[case]()
     x = torch.from_numpy(np.ascontiguousarray(xyz)).cuda()
