@@ -319,11 +319,16 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         SPH_TRY(ensure(g->tcount, nrow * sizeof(int), s));
         SPH_TRY(ensure(g->toff, (nrow + 1) * sizeof(long long), s));
         SPH_TRY(ensure(g->tiles, ntiles_max * sizeof(int4), s));
-        SPH_TRY(ensure(g->tstate, ntiles_max * sizeof(unsigned long long), s));
+        // look-back state of the search (ntiles_max entries), then of the
+        // tile-list builder's chunks of rows (at most nrow + 1), cleared at once
+        const long long nstate = ntiles_max + nrow + 1;
+        SPH_TRY(ensure(g->tstate, nstate * sizeof(unsigned long long), s));
+        SPH_CUDA(cudaMemsetAsync(g->tstate.p, 0, nstate * sizeof(unsigned long long), s));
+        unsigned long long *tstate = P<unsigned long long>(g->tstate);
         d = make_dev(g);
         SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), false, P<int>(g->tcount),
-                              P<long long>(g->toff),
-                              g->scan_tmp.p, P<int4>(g->tiles), g->sm_count, s));
+                              P<long long>(g->toff), g->scan_tmp.p, P<int4>(g->tiles), tstate + ntiles_max,
+                              g->sm_count, s));
         // neighbours per particle: the last measured value, else the
         // uniform-density estimate (particles per cell x the search sphere's
         // volume in cells)
@@ -335,7 +340,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         TileLaunch tv = tile_choose(nbr, g->tile_shape);
         if (g->staging >= 0) tv.extra = g->staging;
         SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell,
-                                  col, col_capacity, rho, P<unsigned long long>(g->tstate), tv, g->sm_count, s));
+                                  col, col_capacity, rho, tstate, tv, true, g->sm_count, s));
     } else {
         SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
         SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));

@@ -341,7 +341,7 @@ static cudaError_t batch_search(sph_batch_s *b, int dim, long long ntot, long lo
     g0.status = P<DevStatus>(b->status);
     return launch_nnps_tile(g0, P<GridDev>(b->gsys), P<int4>(b->tiles), P<long long>(b->toff) + nrow, ntiles_max,
                             reinterpret_cast<long long *>(out->row_ptr), out->col, out->col ? out->col_capacity : 0,
-                            out->rho, P<unsigned long long>(b->tstate), tv, b->sm_count, s);
+                            out->rho, P<unsigned long long>(b->tstate), tv, false, b->sm_count, s);
 }
 
 // Time one launch of the tile search (after a full sequence has prepared its

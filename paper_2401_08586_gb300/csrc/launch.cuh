@@ -66,11 +66,14 @@ cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, lo
 
 // Single-pass search, one warp per row tile (nnps_tile.cu).
 // need_cell_x: compute scell_x from scell first (binning already wrote it
-// for grids; the no-allocation path keeps its own copy).
+// for grids; the no-allocation path keeps its own copy).  cstate (nrow + 1
+// zeroed entries, or nullptr): build the list in one launch with a
+// look-back over chunks of rows instead of count, scan and write.
 cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
-                         long long *toff, void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s);
-// Shared-memory shape of a tile-search launch: TILE_SPARSE (768 kept
-// candidates per pass, 16 warps per SM) or TILE_DENSE (1024, 13 per SM), and
+                         long long *toff, void *scan_tmp, int4 *tiles, unsigned long long *cstate, int sm_count,
+                         cudaStream_t s);
+// Shared-memory shape of a tile-search launch: TILE_SPARSE (672 kept
+// candidates per pass, 20 warps per SM) or TILE_DENSE (832, 16 per SM), and
 // extra dynamic shared memory for output staging.
 enum { TILE_SPARSE = 0, TILE_DENSE = 1 };
 struct TileLaunch {
@@ -79,7 +82,7 @@ struct TileLaunch {
 };
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
-                             unsigned long long *tstate, TileLaunch v, int sm_count, cudaStream_t s);
+                             unsigned long long *tstate, TileLaunch v, bool zeroed, int sm_count, cudaStream_t s);
 // Shape (shape < 0: chosen from nbr) and staging for about nbr neighbours per particle.
 TileLaunch tile_choose(double neighbours_per_particle, int shape);
 

@@ -103,10 +103,10 @@ extern "C" int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t 
     // the tile ticket counter must start at zero; the look-back state is
     // cleared by the launcher; everything else is fully rewritten
     reset_counters_async(d.status, s);
-    cudaError_t e = launch_tiles(d, v.scell, scell_x, true, tcount, toff, scan_tmp, tiles, v.sm_count, s);
+    cudaError_t e = launch_tiles(d, v.scell, scell_x, true, tcount, toff, scan_tmp, tiles, nullptr, v.sm_count, s);
     if (e == cudaSuccess)
         e = launch_nnps_tile(d, nullptr, tiles, toff + v.nrow, ntiles_max, reinterpret_cast<long long *>(row_ptr), col,
-                             col_capacity, rho, tstate, tile_choose(0.0, TILE_SPARSE), v.sm_count, s);
+                             col_capacity, rho, tstate, tile_choose(0.0, TILE_SPARSE), false, v.sm_count, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(SPH_ERR_CUDA, cudaGetErrorString(e));

@@ -729,6 +729,73 @@ __global__ void __launch_bounds__(ROWTILE_NT) k_row_tiles(GridDev g, int *__rest
     }
 }
 
+// Row tiles in one launch: each block takes chunks of whole rows in ticket
+// order (cstate[nchunks] is the ticket), counts their tiles with the rows'
+// cell starts staged in shared memory, finds the chunk's first tile by a
+// decoupled look-back over earlier chunks (cstate[chunk]), and writes the
+// row offsets toff and the tiles.  cstate[0 .. nchunks] must be zero.
+__global__ void __launch_bounds__(ROWTILE_NT) k_row_tiles_lb(GridDev g, long long *__restrict__ toff,
+                                                             int4 *__restrict__ tiles, bool span_limited,
+                                                             unsigned long long *__restrict__ cstate) {
+    __shared__ int cs_s[ROWTILE_SMEM_INTS];
+    __shared__ long long wsum[ROWTILE_NT / 32];
+    __shared__ long long chunk_pre;
+    __shared__ unsigned long long chunk_id;
+    static_assert(ROWTILE_NT == 64, "two warps per block");
+    const long long nrow = (long long)g.nk[1] * g.nk[2];
+    const int nx = g.nk[0];
+    const bool staged = nx + 1 <= ROWTILE_SMEM_INTS;
+    const int rpc = staged ? min(ROWTILE_NT, (ROWTILE_SMEM_INTS - 1) / nx) : ROWTILE_NT;  // rows per chunk
+    const long long nch = (nrow + rpc - 1) / rpc;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    while (true) {
+        __syncthreads();  // the previous chunk is done with the shared buffers
+        if (threadIdx.x == 0) chunk_id = atomicAdd(&cstate[nch], 1ull);
+        __syncthreads();
+        const long long ch = (long long)chunk_id;
+        if (ch >= nch) break;
+        const long long r0 = ch * rpc;
+        const int rows = (int)min((long long)rpc, nrow - r0);
+        const int *cs = g.cell_start + r0 * nx;
+        if (staged) {
+            for (int k = threadIdx.x; k <= rows * nx; k += ROWTILE_NT) cs_s[k] = cs[k];
+            __syncthreads();
+            cs = cs_s;
+        }
+        const int *row = cs + (long long)threadIdx.x * nx;
+        const int cnt = threadIdx.x < rows ? row_tile_count(row, nx, span_limited) : 0;
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int up = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += up;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        const long long total = wsum[0] + wsum[1];
+        const long long rex = (w > 0 ? wsum[0] : 0) + inc - cnt;  // the row's first tile within the chunk
+        if (w == 0) {
+            look_back_publish(cstate, ch, total);
+            const long long pre = look_back_resolve(cstate, ch, total, &g.status->flags);
+            if (lane == 0) chunk_pre = pre;
+        }
+        __syncthreads();
+        const long long pre = chunk_pre;
+        if (threadIdx.x < rows) {
+            const long long r = r0 + threadIdx.x;
+            long long o = pre + rex;
+            toff[r] = o;
+            int c = 0;
+            for (int p = row[0]; p < row[nx];) {
+                const int e = span_limited ? row_tile_end(row, nx, p, c) : min(p + TW, row[nx]);
+                tiles[o++] = make_int4(p, e - p, (int)r, 0);
+                p = e;
+            }
+        }
+        if (ch == nch - 1 && threadIdx.x == 0) toff[nrow] = pre + total;
+    }
+}
+
 // Cell x of every sorted particle.
 __global__ void k_cell_x(GridDev g, const int *__restrict__ scell, int *__restrict__ sx) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += (long long)gridDim.x * blockDim.x)
@@ -753,7 +820,7 @@ static_assert(fits_cta<TileSparse>() && fits_cta<TileDense>(), "shared memory pe
 template <class C>
 cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                          long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
-                         unsigned long long *tstate, int extra_smem, int sm_count, cudaStream_t s) {
+                         unsigned long long *tstate, int extra_smem, bool zeroed, int sm_count, cudaStream_t s) {
     using SM = TileSmem<C>;
     extra_smem = (extra_smem + 15) & ~15;  // keeps every warp's area 16-byte aligned
     const size_t warp_bytes = sizeof(SM) + (size_t)extra_smem;
@@ -778,9 +845,11 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
     long long blocks = (long long)sm_count * per_sm;
     if (blocks > (ntiles_max + C::WPB - 1) / C::WPB) blocks = (ntiles_max + C::WPB - 1) / C::WPB;
     if (blocks < 1) blocks = 1;
-    cudaError_t e =
-        cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
+    if (!zeroed) {
+        const cudaError_t e =
+            cudaMemsetAsync(tstate, 0, (size_t)(ntiles_max > 0 ? ntiles_max : 1) * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
     const int stg_slots = (int)((SM::staging_bytes() + (size_t)extra_smem) / 2);
     ProfScope ps(TAG_FUSED, s);
     note_launch(1);
@@ -792,9 +861,12 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
 }  // namespace
 
 // Build the tile list of a binned grid.  tcount: int[nrow], toff: int64[nrow+1],
-// tiles: int4[ntiles_max] with ntiles_max = n / 32 + nrow.
+// tiles: int4[ntiles_max] with ntiles_max = n / 32 + nrow.  cstate != nullptr:
+// one launch with a look-back over chunks of rows (cstate: nrow + 1 zeroed
+// entries; tcount and scan_tmp unused), else count, scan and write.
 cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
-                         long long *toff, void *scan_tmp, int4 *tiles, int sm_count, cudaStream_t s) {
+                         long long *toff, void *scan_tmp, int4 *tiles, unsigned long long *cstate, int sm_count,
+                         cudaStream_t s) {
     // the no-allocation path (need_cell_x) keeps plain runs of TW particles
     const bool span_limited = !need_cell_x;
     const long long nrow = (long long)g.nk[1] * g.nk[2];
@@ -811,6 +883,13 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
     const long long rpc = nx + 1 <= ROWTILE_SMEM_INTS ? std::min<long long>(ROWTILE_NT, (ROWTILE_SMEM_INTS - 1) / nx)
                                                       : ROWTILE_NT;
     long long rb = (nrow + rpc - 1) / rpc;
+    if (cstate != nullptr) {
+        if (rb > (long long)sm_count * 4) rb = (long long)sm_count * 4;
+        if (rb < 1) rb = 1;
+        note_launch(1);
+        k_row_tiles_lb<<<(unsigned)rb, ROWTILE_NT, 0, s>>>(g, toff, tiles, span_limited, cstate);
+        return cudaGetLastError();
+    }
     if (rb > (long long)sm_count * 16) rb = (long long)sm_count * 16;
     if (rb < 1) rb = 1;
     note_launch(2);
@@ -822,20 +901,21 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
 }
 
 // ntiles_dev: device pointer to the tile count (the last entry of the row
-// tile offsets); ntiles_max bounds it (sizes the look-back state).
+// tile offsets); ntiles_max bounds it (sizes the look-back state, which the
+// launch clears unless the caller already has: zeroed).
 // gsys != nullptr: batch tiles (td.w = system), g then carries the status
 // record and the total particle count.  v: shared-memory shape and extra
 // dynamic shared memory (all of it staging area for the tile's output).
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
-                             unsigned long long *tstate, TileLaunch v, int sm_count, cudaStream_t s) {
+                             unsigned long long *tstate, TileLaunch v, bool zeroed, int sm_count, cudaStream_t s) {
     if (v.extra < 0 || v.extra > TILE_MAX_EXTRA_SMEM || (v.shape != TILE_SPARSE && v.shape != TILE_DENSE))
         return cudaErrorInvalidValue;
     if (v.shape == TILE_DENSE)
         return launch_shape<TileDense>(g, gsys, tiles, ntiles_dev, ntiles_max, row_ptr, col, cap, rho, tstate,
-                                       v.extra, sm_count, s);
+                                       v.extra, zeroed, sm_count, s);
     return launch_shape<TileSparse>(g, gsys, tiles, ntiles_dev, ntiles_max, row_ptr, col, cap, rho, tstate, v.extra,
-                                    sm_count, s);
+                                    zeroed, sm_count, s);
 }
 
 // Shape and staging for a grid whose rows hold about `nbr` neighbours on
