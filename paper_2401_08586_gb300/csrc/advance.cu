@@ -119,7 +119,7 @@ cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *
 cudaError_t launch_advance(const GridDev &g, const int *scell, const double4 *rel64, const double *vel, double dt,
                            int *cnt, int *cid, int *slot, uint2 *rel16u, float4 *rel32u, double4 *rel64u,
                            int sm_count, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)g.ncell * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, cnt_bytes(g.ncell), s);  // counters and their scan state
     if (e != cudaSuccess) return e;
     ProfScope ps(TAG_HASH, s);
     note_launch(1);

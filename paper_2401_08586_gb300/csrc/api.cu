@@ -180,7 +180,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
         const long long nn = n > 0 ? n : 1;
         const long long big = ncell > nn ? ncell : nn;
         if ((rc = ensure(g->cell_start, (ncell + 1) * sizeof(int), s)) ||
-            (rc = ensure(g->cnt, ncell * sizeof(int), s)) || (rc = ensure(g->cid, nn * sizeof(int), s)) ||
+            (rc = ensure(g->cnt, cnt_bytes(ncell), s)) || (rc = ensure(g->cid, nn * sizeof(int), s)) ||
             (rc = ensure(g->slot, nn * sizeof(int), s)) || (rc = ensure(g->orig_id, nn * sizeof(int), s)) ||
             (rc = ensure(g->rank, nn * sizeof(int), s)) || (rc = ensure(g->scell, nn * sizeof(int), s)) ||
             (rc = ensure(g->scan_tmp, scan_tmp_bytes(big + 1), s)) ||

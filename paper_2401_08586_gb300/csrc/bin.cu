@@ -214,7 +214,9 @@ cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int
                                  int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
-    cudaError_t e = exclusive_scan_i32(cnt, cell_start, g.ncell, scan_tmp, s);
+    // cnt is followed by the zeroed look-back state of its scan
+    cudaError_t e =
+        exclusive_scan_i32_lb(cnt, cell_start, g.ncell, cnt_scan_state(cnt, g.ncell), &g.status->flags, sm_count, s);
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(TAG_SCATTER, s);
@@ -241,7 +243,7 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
                                         unsigned int *big_count, int check_box, int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
-    cudaError_t e = cudaMemsetAsync(cnt, 0, g.ncell * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, cnt_bytes(g.ncell), s);  // counters and their scan state
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(TAG_HASH, s);

@@ -17,7 +17,9 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
                                         int check_box, int sm_count, cudaStream_t s);
 // Scan of the cell histogram, scatter, per-cell sort and the gather of the
 // input-order arrays (cid, rel16u, rel32u and, if not NULL, rel64u) into
-// cell order: the second half of binning, shared with the time step.
+// cell order: the second half of binning, shared with the time step.  cnt
+// has cnt_bytes(ncell) bytes, cleared (with its scan state) before the
+// histogram was counted.
 cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
                                  int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
                                  const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,

@@ -36,11 +36,13 @@
 #include <mutex>
 
 #include "launch.cuh"
+#include "lookback.cuh"
 #include "nnps_common.cuh"
 
 namespace sph {
 
 using namespace nn;
+using namespace lb;
 
 namespace {
 
@@ -71,10 +73,6 @@ struct TileCfg {
 using TileSparse = TileCfg<672, 192, 2, 20>;
 using TileDense = TileCfg<832, 256, 2, 16>;
 
-constexpr unsigned long long ST_AGG = 1ull << 62;
-constexpr unsigned long long ST_INCL = 2ull << 62;
-constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
-constexpr int LOOKBACK_SPIN_LIMIT = 1 << 20;
 
 template <class C>
 struct TileSmem {
@@ -94,9 +92,6 @@ struct TileSmem {
     static constexpr size_t staging_bytes() { return sizeof(code) + sizeof(pw) + sizeof(f32); }
 };
 
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
@@ -112,55 +107,6 @@ __device__ __forceinline__ float w_poly_bf(float R) {
     const float w2 = t * t * t * (1.f / 6.f);
     const float w1 = fmaf(R * R, fmaf(0.5f, R, -1.f), 2.f / 3.f);
     return R < 1.f ? w1 : w2;
-}
-
-// Publish this tile's total (an aggregate, or already the inclusive prefix
-// for tile 0).  Successors can use it before this tile has resolved its own
-// prefix.
-__device__ __forceinline__ void look_back_publish(unsigned long long *tstate, long long t, long long agg) {
-    if ((threadIdx.x & 31) == 0)
-        atomicExch(&tstate[t], (t == 0 ? ST_INCL : ST_AGG) | (unsigned long long)agg);
-}
-
-// Sum of all earlier tiles' totals, by looking back over their published
-// states 32 at a time (stopping at the first inclusive prefix); then publish
-// this tile's inclusive prefix.  Every wait is bounded: after
-// LOOKBACK_SPIN_LIMIT polls the tile records ST_TIMEOUT and continues.
-__device__ __forceinline__ long long look_back_resolve(unsigned long long *tstate, long long t, long long agg,
-                                                       unsigned int *flags) {
-    const int lane = threadIdx.x & 31;
-    if (t == 0) return 0;
-    long long excl = 0, j = t - 1;
-    int spins = 0, backoff = 32;
-    bool timed_out = false;
-    while (true) {
-        const long long idx = j - lane;
-        const unsigned long long s = idx >= 0 ? ld_volatile(&tstate[idx]) : ST_INCL;
-        const unsigned int flag = (unsigned int)(s >> 62);
-        const unsigned int m2 = __ballot_sync(0xffffffffu, flag == 2u);
-        const unsigned int m0 = __ballot_sync(0xffffffffu, flag == 0u);
-        const int stop = m2 ? __ffs(m2) - 1 : 31;
-        const unsigned int need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
-        if (m0 & need) {
-            if (++spins > LOOKBACK_SPIN_LIMIT) {
-                timed_out = true;
-                break;
-            }
-            __nanosleep(backoff);
-            backoff = min(backoff * 2, 1024);
-            continue;
-        }
-        long long v = lane <= stop ? (long long)(s & ST_VAL) : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        excl += v;
-        if (m2) break;
-        j -= 32;
-        backoff = 32;
-    }
-    if (timed_out && lane == 0) atomicOr(flags, ST_TIMEOUT);
-    if (lane == 0) atomicExch(&tstate[t], ST_INCL | (unsigned long long)(excl + agg));
-    return excl;
 }
 
 __device__ __forceinline__ float warp_min(float v) {

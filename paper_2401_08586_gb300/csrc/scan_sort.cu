@@ -2,13 +2,15 @@
 // counting sort of the binning step and by the CSR assembly.
 //
 // Scan: one launch of one block up to SCAN_SMALL_MAX items, else three
-// launches (tile sums, scan of tile sums, tile scan + offset).
+// launches (tile sums, scan of tile sums, tile scan + offset), or, given a
+// zeroed state array, one launch with a decoupled look-back over tiles.
 // Sort: every segment is sorted ascending with a bitonic network written so
 // that all comparators put the minimum at the lower index (the first step of
 // each merge compares i with i ^ (k - 1)).  With that form, positions past the
 // segment end behave as +infinity and are simply skipped, so no padding is
 // stored.  Segments of <= 32 keys are sorted in registers by one warp,
 // <= 1024 keys by one warp in shared memory, larger ones by a whole block.
+#include "lookback.cuh"
 #include "profile.cuh"
 #include "sph_internal.cuh"
 
@@ -142,6 +144,56 @@ __global__ void __launch_bounds__(SMALL_NT) k_scan_small(const int *__restrict__
         ex += in[i];
     }
     if (threadIdx.x == 0) out[n] = (OutT)total;
+}
+
+// Single-launch scan: blocks take tiles of SCAN_TILE items in ticket order
+// (state[ntile] is the ticket), scan them in shared memory and add the
+// prefix of all earlier tiles found by a decoupled look-back (state[tile]).
+template <typename OutT>
+__global__ void __launch_bounds__(SCAN_NT) k_scan_lb(const int *__restrict__ in, OutT *__restrict__ out, long long n,
+                                                      unsigned long long *__restrict__ state, long long ntile,
+                                                      unsigned int *flags) {
+    __shared__ long long buf[SCAN_TILE];
+    __shared__ long long tile_pre;
+    __shared__ unsigned long long tile_id;
+    while (true) {
+        __syncthreads();  // the previous tile is done with the shared buffers
+        if (threadIdx.x == 0) tile_id = atomicAdd(&state[ntile], 1ull);
+        __syncthreads();
+        const long long t = (long long)tile_id;
+        if (t >= ntile) break;
+        const long long base = t * SCAN_TILE;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            const long long idx = base + (long long)k * SCAN_NT + threadIdx.x;
+            buf[k * SCAN_NT + threadIdx.x] = idx < n ? in[idx] : 0;
+        }
+        __syncthreads();
+        long long own[SCAN_ITEMS];
+        long long sum = 0;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            own[k] = buf[threadIdx.x * SCAN_ITEMS + k];
+            sum += own[k];
+        }
+        long long tot;
+        long long ex = block_excl_scan_256(sum, &tot);
+        if (threadIdx.x < 32) {
+            lb::look_back_publish(state, t, tot);
+            const long long pre = lb::look_back_resolve(state, t, tot, flags);
+            if (threadIdx.x == 0) tile_pre = pre;
+        }
+        __syncthreads();
+        ex += tile_pre;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            buf[threadIdx.x * SCAN_ITEMS + k] = ex;
+            ex += own[k];
+        }
+        __syncthreads();
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            const long long idx = base + (long long)k * SCAN_NT + threadIdx.x;
+            if (idx < n) out[idx] = (OutT)buf[k * SCAN_NT + threadIdx.x];
+        }
+        if (t == ntile - 1 && threadIdx.x == 0) out[n] = (OutT)(tile_pre + tot);
+    }
 }
 
 template <typename OutT>
@@ -281,6 +333,19 @@ size_t scan_tmp_bytes(long long n) {
     long long ntile = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntile == 0) ntile = 1;
     return (size_t)(ntile + 1) * sizeof(long long);
+}
+
+long long scan_lb_state_entries(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+cudaError_t exclusive_scan_i32_lb(const int *in, int *out, long long n, unsigned long long *state,
+                                  unsigned int *flags, int sm_count, cudaStream_t s) {
+    const long long ntile = scan_lb_state_entries(n) - 1;
+    if (ntile <= 1) return exclusive_scan_i32(in, out, n, nullptr, s);  // one block: no look-back needed
+    long long blocks = ntile < (long long)sm_count * 4 ? ntile : (long long)sm_count * 4;
+    ProfScope ps(TAG_SCAN, s);
+    note_launch(1);
+    k_scan_lb<int><<<(unsigned)blocks, SCAN_NT, 0, s>>>(in, out, n, state, ntile, flags);
+    return cudaGetLastError();
 }
 
 cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t s) {

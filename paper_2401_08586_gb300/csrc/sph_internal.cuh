@@ -187,6 +187,21 @@ constexpr long long SCAN_SMALL_MAX = 1LL << 14;  // scans this short run in one 
 cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t s);
 cudaError_t exclusive_scan_i64(const int *in, long long *out, long long n, void *tmp,
                                cudaStream_t s);
+// The same in one launch (decoupled look-back over tiles of the input):
+// state holds scan_lb_state_entries(n) entries, all zero at the launch; a
+// bounded wait that runs out sets ST_TIMEOUT in *flags.
+long long scan_lb_state_entries(long long n);
+cudaError_t exclusive_scan_i32_lb(const int *in, int *out, long long n, unsigned long long *state,
+                                  unsigned int *flags, int sm_count, cudaStream_t s);
+// A grid's cell counters are followed by the look-back state of their scan,
+// so that the one memset that clears the counters clears the state too.
+inline long long cnt_words(long long ncell) { return (ncell + 1) & ~1LL; }  // keeps the state 8-byte aligned
+inline size_t cnt_bytes(long long ncell) {
+    return (size_t)cnt_words(ncell) * sizeof(int) + (size_t)scan_lb_state_entries(ncell) * 8;
+}
+inline unsigned long long *cnt_scan_state(int *cnt, long long ncell) {
+    return reinterpret_cast<unsigned long long *>(cnt + cnt_words(ncell));
+}
 
 // Sort every segment [seg_start[c], seg_start[c+1]) of keys ascending, for
 // c < nseg.  Segments longer than 32 are listed in big_list (capacity nseg)
