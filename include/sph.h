@@ -268,6 +268,18 @@ int sph_grid_info_get(sph_grid_t grid, sph_grid_info *info);
 int sph_grid_export(sph_grid_t grid, int32_t *orig_id, int32_t *rank, int32_t *cell_start,
                     void *stream);
 
+/* Copy the stored cell-relative coordinates (Eq. 6, SPH_PREC_FP16_RCLL grids
+ * only) in sorted order into caller buffers (device memory, either may be
+ * NULL): rel16 uint16[n][4] (FP16 bit patterns x, y, z, 0), rel32 float[n][4]
+ * (x, y, z, 0).  Units u = h_c / 2 relative to the centre of the particle's
+ * cell: for s = 2 (x - lo) / h_c rounded to FP64 (one fused multiply-add
+ * when every coordinate lies within 2^17 u of the origin, else a subtraction
+ * and a multiplication) and c = min(floor(s / 2), n_k - 1), the FP32 value is
+ * s - (2c + 1) rounded to nearest and the FP16 value is the FP32 value
+ * rounded to nearest.  Enqueued on `stream`.  SPH_ERR_INVALID for other
+ * precisions. */
+int sph_grid_export_rel(sph_grid_t grid, uint16_t *rel16, float *rel32, void *stream);
+
 /* Synchronise `stream` and report any error a device-side check recorded for
  * this grid since the last synchronising call (SPH_OK if none). */
 int sph_grid_check(sph_grid_t grid, void *stream);

@@ -490,6 +490,18 @@ extern "C" int sph_grid_export(sph_grid_t grid, int32_t *orig_id, int32_t *rank,
     return SPH_OK;
 }
 
+extern "C" int sph_grid_export_rel(sph_grid_t grid, uint16_t *rel16, float *rel32, void *stream) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (g->p.precision != SPH_PREC_FP16_RCLL) return fail(SPH_ERR_INVALID, "the grid stores no relative coordinates");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (rel16 && g->n)
+        SPH_CUDA(cudaMemcpyAsync(rel16, g->rel16.p, g->n * sizeof(uint2), cudaMemcpyDeviceToDevice, s));
+    if (rel32 && g->n)
+        SPH_CUDA(cudaMemcpyAsync(rel32, g->rel32.p, g->n * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+    return SPH_OK;
+}
+
 extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
     sph_grid_s *g = grid;
     if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");

@@ -100,8 +100,8 @@ __global__ void k_bounds(const double *__restrict__ xyz, long long total, int di
     }
 }
 
-template <int PREC>
-__global__ void k_hash(const double *__restrict__ xyz, int n, int dim, GridDev g,
+template <int PREC, int DIM>
+__global__ void k_hash(const double *__restrict__ xyz, int n, GridDev g,
                        int *__restrict__ cnt, int *__restrict__ cid, int *__restrict__ slot,
                        uint2 *__restrict__ rel16u, float4 *__restrict__ rel32u, int check_box) {
     const int lane = threadIdx.x & 31;
@@ -113,23 +113,30 @@ __global__ void k_hash(const double *__restrict__ xyz, int n, int dim, GridDev g
         if (live) {
             int cc[3] = {0, 0, 0};
             double a[3] = {0.0, 0.0, 0.0};
-            if (g.fma_bin) {
-                for (int k = 0; k < dim; ++k)
-                    cc[k] = rel_axis_fma(xyz[i * dim + k], g.neg_lo_t[k], g.two_over_hc, g.nk[k], a[k]);
-            } else {
-                for (int k = 0; k < dim; ++k)
-                    cc[k] = rel_axis(xyz[i * dim + k], g.lo[k], g.two_over_hc, g.nk[k], a[k]);
+            float fr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const double x = xyz[i * DIM + k];
+                if (g.fma_bin) {
+                    const double sk = __fma_rn(x, g.two_over_hc, g.neg_lo_t[k]);
+                    // without a box check the FP64 relative coordinate itself is not needed
+                    if (!check_box && rel_axis_bits(sk, g.nk[k], cc[k], fr[k])) continue;
+                    cc[k] = rel_axis_s(sk, g.nk[k], a[k]);
+                } else {
+                    cc[k] = rel_axis(x, g.lo[k], g.two_over_hc, g.nk[k], a[k]);
+                }
+                fr[k] = __double2float_rn(a[k]);
             }
             if (check_box) {
                 bool out = false;
-                for (int k = 0; k < dim; ++k) out |= fabs(a[k]) > 1.0 + 1e-6;
+                for (int k = 0; k < DIM; ++k) out |= fabs(a[k]) > 1.0 + 1e-6;
                 if (out) atomicOr(&g.status->flags, ST_OUT_OF_BOX);
             }
             c = (cc[2] * g.nk[1] + cc[1]) * g.nk[0] + cc[0];
             if (PREC == SPH_PREC_FP16_RCLL) {
                 uint2 q;
                 float4 f;
-                round_rel(a, q, f);
+                round_rel_f(fr[0], fr[1], fr[2], q, f);
                 rel16u[i] = q;
                 rel32u[i] = f;
             }
@@ -248,12 +255,10 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
     {
         ProfScope ps(TAG_HASH, s);
         note_launch(1);
-        if (prec == SPH_PREC_FP16_RCLL)
-            k_hash<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot, rel16u, rel32u,
-                                                             check_box);
-        else
-            k_hash<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(xyz, n, dim, g, cnt, cid, slot, nullptr, nullptr,
-                                                            check_box);
+        const bool r = prec == SPH_PREC_FP16_RCLL;
+        auto kern = r ? (dim == 2 ? k_hash<SPH_PREC_FP16_RCLL, 2> : k_hash<SPH_PREC_FP16_RCLL, 3>)
+                      : (dim == 2 ? k_hash<SPH_PREC_FP64_CLL, 2> : k_hash<SPH_PREC_FP64_CLL, 3>);
+        kern<<<blocks, nt, 0, s>>>(xyz, n, g, cnt, cid, slot, r ? rel16u : nullptr, r ? rel32u : nullptr, check_box);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

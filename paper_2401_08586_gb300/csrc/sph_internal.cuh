@@ -130,17 +130,55 @@ __device__ __forceinline__ int rel_axis_fma(double x, double neg_lo_t, double tw
     return rel_axis_s(__fma_rn(x, two_over_hc, neg_lo_t), nk, a);
 }
 
+// RN32(v 2^-sh) for |v| < 2^63 and 32 <= sh <= 62 with 32-bit conversions
+// only: v is normalised so that its leading one is bit 63, every bit below
+// the top 32 is ORed into the lowest of them (sticky), and the 32-bit value
+// is converted; the FP32 rounding looks at no more than the 8 bits below its
+// 24, so the sticky bit gives the rounding of the full value.  The power-of-
+// two scale is exact (the result stays a normal float).
+__device__ __forceinline__ float i64_scaled_to_f32_rn(long long v, int sh) {
+    const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = u >> 32 ? __clzll(u) : 32;
+    const unsigned long long t = u << lz;  // lz = 32 when u fits 32 bits: exact
+    const unsigned int hi = (unsigned int)(t >> 32) | ((unsigned int)t != 0u ? 1u : 0u);
+    const float r = __uint2float_rn(hi) * __int_as_float((127 + 32 - lz - sh) << 23);
+    return v < 0 ? -r : r;
+}
+
+// The same cell and the FP32 relative coordinate RN32(s - (2c + 1)) from the
+// bits of s, for 2^-10 <= s < 2^21 (false otherwise: the caller takes the
+// FP64 route).  With s = m 2^(e - 52) (m the 53-bit significand), floor(s) =
+// m >> (52 - e) and s - (2c + 1) = A 2^(e - 52) exactly, A = m - ((2c + 1) <<
+// (52 - e)) with |A| < 2^62, rounded to the nearest FP32 (even on ties) and
+// scaled exactly, so the result is bit-identical to rel_axis_s followed by
+// the FP32 rounding, without FP64 conversions or subtraction (FP64 issue is
+// the slow path on this part).
+__device__ __forceinline__ bool rel_axis_bits(double s, int nk, int &c, float &f) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    const int e = (int)(b >> 52) - 1023;  // the sign bit makes e >= 1025 - 1023 for s < 0
+    if (e < -10 || e > 20) return false;
+    const unsigned long long m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+    const int sh = 52 - e;  // 32 .. 62
+    const long long fl = (long long)(m >> sh);
+    c = (int)min(fl >> 1, (long long)(nk - 1));
+    const long long A = (long long)m - ((long long)(2 * c + 1) << sh);
+    f = i64_scaled_to_f32_rn(A, sh);
+    return true;
+}
+
 // The stored relative coordinates: FP32 rounded once from the FP64 value,
 // FP16 rounded from the FP32 value.  The second rounding adds at most 2^-25
 // u to the FP16 coordinate's error (2^-12 u for |x_rel| <= 1), far inside the
 // FP16 band's margin.
-__device__ __forceinline__ void round_rel(const double a[3], uint2 &q16, float4 &f32) {
-    const float f0 = __double2float_rn(a[0]), f1 = __double2float_rn(a[1]), f2 = __double2float_rn(a[2]);
+__device__ __forceinline__ void round_rel_f(float f0, float f1, float f2, uint2 &q16, float4 &f32) {
     const __half2 xy = __floats2half2_rn(f0, f1);
     const __half2 z0 = __floats2half2_rn(f2, 0.f);
     q16.x = *reinterpret_cast<const unsigned int *>(&xy);
     q16.y = *reinterpret_cast<const unsigned int *>(&z0);
     f32 = make_float4(f0, f1, f2, 0.f);
+}
+__device__ __forceinline__ void round_rel(const double a[3], uint2 &q16, float4 &f32) {
+    round_rel_f(__double2float_rn(a[0]), __double2float_rn(a[1]), __double2float_rn(a[2]), q16, f32);
 }
 
 // Row tiles of the single-pass search: runs of at most TILE_ROWS

@@ -125,6 +125,7 @@ def load(build_if_missing=False):
         "sph_density_sum": [_vp, _vp, _vp, _vp, _vp],
         "sph_grid_info_get": [_vp, ctypes.POINTER(sph_grid_info)],
         "sph_grid_export": [_vp, _vp, _vp, _vp, _vp],
+        "sph_grid_export_rel": [_vp, _vp, _vp, _vp],
         "sph_grid_check": [_vp, _vp],
         "sph_grid_free": [_vp],
         "sph_last_error": [],
@@ -172,7 +173,7 @@ def load(build_if_missing=False):
 def exported_symbols():
     """Names of the C-ABI entry points this binding expects."""
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
-            "sph_grid_export", "sph_grid_check", "sph_grid_free", "sph_last_error",
+            "sph_grid_export", "sph_grid_export_rel", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
@@ -249,6 +250,10 @@ def sph_grid_info_get(grid):
 
 def sph_grid_export(grid, orig_id=None, rank=None, cell_start=None, stream=None):
     _check(load().sph_grid_export(grid, _ptr(orig_id), _ptr(rank), _ptr(cell_start), _stream(stream)))
+
+
+def sph_grid_export_rel(grid, rel16=None, rel32=None, stream=None):
+    _check(load().sph_grid_export_rel(grid, _ptr(rel16), _ptr(rel32), _stream(stream)))
 
 
 def sph_grid_check(grid, stream=None):
@@ -646,6 +651,15 @@ class Grid:
         out = torch.empty(self.n, dtype=torch.int32, device=self.xyz.device)
         sph_grid_export(self.handle, out, None, None, stream)
         return out
+
+    def relative_coordinates(self, stream=None):
+        """(rel16, rel32) in sorted order: float16[N, 4] and float32[N, 4]
+        tensors of the stored cell-relative coordinates (x, y, z, 0)."""
+        import torch
+        r16 = torch.empty((self.n, 4), dtype=torch.int16, device=self.xyz.device)
+        r32 = torch.empty((self.n, 4), dtype=torch.float32, device=self.xyz.device)
+        sph_grid_export_rel(self.handle, r16, r32, stream)
+        return r16.view(torch.float16), r32
 
     def rank(self, stream=None):
         """int32[N] tensor: input index -> sorted position."""
