@@ -96,8 +96,9 @@ __global__ void k_batch_bounds(const BinSys *__restrict__ sys, int dim, unsigned
 
 // Cell, relative coordinates and warp-aggregated cell histogram of every
 // particle of the batch (as k_hash of a single grid).
+template <int DIM>
 __global__ void k_batch_hash(const BinSys *__restrict__ sys, const long long *__restrict__ first, int nsys,
-                             long long ntot, int dim, int *__restrict__ cnt, int *__restrict__ cid,
+                             long long ntot, int *__restrict__ cnt, int *__restrict__ cid,
                              int *__restrict__ slot, uint2 *__restrict__ rel16u, float4 *__restrict__ rel32u,
                              DevStatus *st) {
     const int lane = threadIdx.x & 31;
@@ -111,16 +112,22 @@ __global__ void k_batch_hash(const BinSys *__restrict__ sys, const long long *__
             const long long i = I - first[s];
             int cc[3] = {0, 0, 0};
             double a[3] = {0.0, 0.0, 0.0};
+            float fr[3] = {0.f, 0.f, 0.f};
             bool out = false;
-            for (int k = 0; k < dim; ++k) {
-                cc[k] = rel_axis(S.xyz[i * dim + k], S.lo[k], S.two_over_hc, S.nk[k], a[k]);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const double sk = __dmul_rn(__dsub_rn(S.xyz[i * DIM + k], S.lo[k]), S.two_over_hc);
+                // without a box check the FP64 relative coordinate itself is not needed
+                if (!S.check_box && rel_axis_bits(sk, S.nk[k], cc[k], fr[k])) continue;
+                cc[k] = rel_axis_s(sk, S.nk[k], a[k]);
                 out |= fabs(a[k]) > 1.0 + 1e-6;
+                fr[k] = __double2float_rn(a[k]);
             }
             if (out && S.check_box) atomicOr(&st->flags, ST_OUT_OF_BOX);
             c = S.cell_base + (cc[2] * S.nk[1] + cc[1]) * S.nk[0] + cc[0];
             uint2 q;
             float4 f;
-            round_rel(a, q, f);
+            round_rel_f(fr[0], fr[1], fr[2], q, f);
             rel16u[I] = q;
             rel32u[I] = f;
         }
@@ -298,8 +305,8 @@ static cudaError_t batch_prep(sph_batch_s *b, int nsys, int dim, long long ntot,
     {
         ProfScope ps(TAG_HASH, s);
         note_launch(1);
-        k_batch_hash<<<grid_blocks(ntot, nt, b->sm_count, 16), nt, 0, s>>>(
-            bsys, first, nsys, ntot, dim, P<int>(b->cnt), P<int>(b->cid), P<int>(b->slot), P<uint2>(b->rel16u),
+        (dim == 2 ? k_batch_hash<2> : k_batch_hash<3>)<<<grid_blocks(ntot, nt, b->sm_count, 16), nt, 0, s>>>(
+            bsys, first, nsys, ntot, P<int>(b->cnt), P<int>(b->cid), P<int>(b->slot), P<uint2>(b->rel16u),
             P<float4>(b->rel32u), st);
     }
     if ((e = exclusive_scan_i32(P<int>(b->cnt), P<int>(b->cell_start), ncell, b->scan_tmp.p, s)) != cudaSuccess)
