@@ -7,21 +7,25 @@
 //              domain extent), finiteness check;
 //   k_hash     cell index c_k = clamp(floor((x_k - lo_k) / h_c), 0, n_k - 1)
 //              and the relative coordinate x_rel = 2 (x - x_cc) / h_c with
-//              x_cc the cell centre, computed in FP64 and rounded once to FP16
-//              and FP32 (input order); linear id (c_z n_y + c_y) n_x + c_x,
+//              x_cc the cell centre, as the FP64 value rounded to FP32 and
+//              then FP16 (input order); linear id (c_z n_y + c_y) n_x + c_x,
 //              warp-aggregated histogram whose returned counter value is the
 //              particle's provisional slot;
 //   (exclusive scan of the histogram -> cell_start)
 //   k_scatter  orig_id[cell_start[cell] + slot] = i;
-//   (per-cell sort of orig_id, so the order inside a cell is the input order
-//    and the result does not depend on atomic timing)
-//   k_convert  for every sorted position: rank, cell id and the relative
-//              coordinates gathered into cell order (rel16, rel32); or, for
-//              the FP64 cell link-list, the FP64 coordinate.
-// The FP64 work is one pass of five operations per axis: this part's FP64
-// rate is a small fraction of its FP32 and integer rates.
+//   k_sort_convert  per cell: orig_id sorted ascending, so the order inside
+//              a cell is the input order and the result does not depend on
+//              atomic timing; then for every sorted position its rank, cell
+//              id and the relative coordinates gathered into cell order
+//              (rel16, rel32), or, for the FP64 cell link-list, the FP64
+//              coordinate.
+// The FP64 work is one fused multiply-add per axis (s = 2 (x - lo) / h_c);
+// the floor, the difference and its FP32 rounding are exact integer work on
+// the bits of s, since this part's FP64 rate is a small fraction of its
+// FP32 and integer rates.
 #include "launch.cuh"
 #include "profile.cuh"
+#include "sortnet.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -161,31 +165,91 @@ __global__ void k_scatter(int n, const int *__restrict__ cell_start, const int *
         orig_id[cell_start[cid[i]] + slot[i]] = (int)i;
 }
 
-// Sorted position s takes input particle i = orig_id[s]: its rank, cell and
-// (RCLL) the relative coordinates computed by k_hash, or (FP64 cell
-// link-list) its FP64 coordinates.
+// Outputs of sorted position s, holding input particle i of cell c (cell x
+// cx): its rank and cell, and (RCLL) the relative coordinates computed by
+// k_hash, or (FP64 cell link-list) its FP64 coordinates.
+struct ConvertOut {
+    int *rank, *scell, *scell_x;
+    uint2 *rel16;
+    float4 *rel32;
+    const uint2 *rel16u;
+    const float4 *rel32u;
+    const double4 *rel64u;
+    double4 *rel64, *x64;
+};
+
 template <int PREC>
-__global__ void k_convert(int n, int dim, GridDev g, const int *__restrict__ cid_in,
-                          int *__restrict__ rank, int *__restrict__ scell, uint2 *__restrict__ rel16,
-                          float4 *__restrict__ rel32, const uint2 *__restrict__ rel16u,
-                          const float4 *__restrict__ rel32u, const double4 *__restrict__ rel64u,
-                          double4 *__restrict__ rel64, double4 *__restrict__ x64, int *__restrict__ scell_x) {
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
-         s += (long long)gridDim.x * blockDim.x) {
-        const int i = g.orig_id[s];
-        rank[i] = (int)s;
-        const int c = cid_in[i];
-        scell[s] = c;
-        if (scell_x != nullptr) scell_x[s] = c - (int)fastdiv_div((uint32_t)c, g.div_nx) * g.nk[0];
-        if (PREC == SPH_PREC_FP64_CLL) {
-            double x[3] = {0.0, 0.0, 0.0};
-            for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];
-            x64[s] = make_double4(x[0], x[1], x[2], 0.0);
-        } else {
-            rel16[s] = rel16u[i];
-            rel32[s] = rel32u[i];
-            if (rel64 != nullptr) rel64[s] = rel64u[i];
+__device__ __forceinline__ void convert_pos(const GridDev &g, int dim, const ConvertOut &o, int s, int i, int c,
+                                            int cx) {
+    o.rank[i] = s;
+    o.scell[s] = c;
+    if (o.scell_x != nullptr) o.scell_x[s] = cx;
+    if (PREC == SPH_PREC_FP64_CLL) {
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];
+        o.x64[s] = make_double4(x[0], x[1], x[2], 0.0);
+    } else {
+        o.rel16[s] = o.rel16u[i];
+        o.rel32[s] = o.rel32u[i];
+        if (o.rel64 != nullptr) o.rel64[s] = o.rel64u[i];
+    }
+}
+
+constexpr int SORTCV_NT = 128;
+constexpr int SORTCV_SMEM_KEYS = 1024;
+
+// Per cell, one warp: sort the cell's input indices (scattered into
+// orig_id in arrival order) ascending -- in registers up to 32, in shared
+// memory up to 1024, longer cells are listed for k_sort_convert_big -- and
+// write every sorted position's outputs.
+template <int PREC>
+__global__ void __launch_bounds__(SORTCV_NT) k_sort_convert(GridDev g, int dim, ConvertOut o, int *__restrict__ keys,
+                                                             const int *__restrict__ cell_start, int *big_list,
+                                                             unsigned int *big_count) {
+    __shared__ int wbuf[SORTCV_NT / 32][SORTCV_SMEM_KEYS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long nw = ((long long)gridDim.x * SORTCV_NT) >> 5;
+    for (long long c = ((long long)blockIdx.x * SORTCV_NT + threadIdx.x) >> 5; c < g.ncell; c += nw) {
+        const int a = cell_start[c], len = cell_start[c + 1] - a;
+        if (len == 0) continue;
+        const int cx = (int)c - (int)fastdiv_div((uint32_t)c, g.div_nx) * g.nk[0];
+        if (len <= 32) {
+            int v = lane < len ? keys[a + lane] : 0;
+            if (len > 1) v = net::warp_sort32(v, lane, len);
+            if (lane < len) {
+                keys[a + lane] = v;
+                convert_pos<PREC>(g, dim, o, a + lane, v, (int)c, cx);
+            }
+        } else if (len <= SORTCV_SMEM_KEYS) {
+            int *buf = wbuf[w];
+            for (int k = lane; k < len; k += 32) buf[k] = keys[a + k];
+            __syncwarp();
+            net::bitonic_all_ascending(buf, len, lane, 32, net::WarpSync());
+            for (int k = lane; k < len; k += 32) {
+                keys[a + k] = buf[k];
+                convert_pos<PREC>(g, dim, o, a + k, buf[k], (int)c, cx);
+            }
+            __syncwarp();
+        } else if (lane == 0) {
+            big_list[atomicAdd(big_count, 1u)] = (int)c;
         }
+    }
+}
+
+// Cells longer than SORTCV_SMEM_KEYS: one block each, sorted in place.
+template <int PREC>
+__global__ void __launch_bounds__(SORTCV_NT) k_sort_convert_big(GridDev g, int dim, ConvertOut o, int *keys,
+                                                                 const int *__restrict__ cell_start,
+                                                                 const int *big_list,
+                                                                 const unsigned int *big_count) {
+    const unsigned int nbig = *big_count;
+    for (unsigned int b = blockIdx.x; b < nbig; b += gridDim.x) {
+        const int c = big_list[b];
+        const int a = cell_start[c], len = cell_start[c + 1] - a;
+        net::bitonic_all_ascending(keys + a, len, threadIdx.x, SORTCV_NT, net::BlockSync());
+        const int cx = c - (int)fastdiv_div((uint32_t)c, g.div_nx) * g.nk[0];
+        for (int k = threadIdx.x; k < len; k += SORTCV_NT) convert_pos<PREC>(g, dim, o, a + k, keys[a + k], c, cx);
+        __syncthreads();
     }
 }
 
@@ -230,16 +294,28 @@ cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int
         note_launch(1);
         k_scatter<<<blocks, nt, 0, s>>>(n, cell_start, cid, slot, orig_id);
     }
-    e = segmented_sort_i32(orig_id, cell_start, g.ncell, big_list, big_count, s);
+    // per cell: sort its input indices and write the sorted positions' outputs
+    e = cudaMemsetAsync(big_count, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    ProfScope ps(TAG_CONVERT, s);
-    note_launch(1);
-    if (prec == SPH_PREC_FP16_RCLL)
-        k_convert<SPH_PREC_FP16_RCLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, rel16, rel32, rel16u,
-                                                            rel32u, rel64u, rel64, nullptr, scell_x);
-    else
-        k_convert<SPH_PREC_FP64_CLL><<<blocks, nt, 0, s>>>(n, dim, g, cid, rank, scell, nullptr, nullptr, nullptr,
-                                                           nullptr, nullptr, nullptr, x64, scell_x);
+    ProfScope ps(TAG_SORT, s);
+    note_launch(2);
+    const bool r = prec == SPH_PREC_FP16_RCLL;
+    const ConvertOut o{rank,  scell, scell_x, r ? rel16 : nullptr, r ? rel32 : nullptr, rel16u, rel32u,
+                       rel64u, r ? rel64 : nullptr, r ? nullptr : x64};
+    long long sb = (g.ncell * 32 + SORTCV_NT - 1) / SORTCV_NT;
+    if (sb > (long long)sm_count * 16) sb = (long long)sm_count * 16;
+    if (sb < 1) sb = 1;
+    if (r) {
+        k_sort_convert<SPH_PREC_FP16_RCLL><<<(unsigned)sb, SORTCV_NT, 0, s>>>(g, dim, o, orig_id, cell_start,
+                                                                              big_list, big_count);
+        k_sort_convert_big<SPH_PREC_FP16_RCLL><<<sm_count, SORTCV_NT, 0, s>>>(g, dim, o, orig_id, cell_start,
+                                                                              big_list, big_count);
+    } else {
+        k_sort_convert<SPH_PREC_FP64_CLL><<<(unsigned)sb, SORTCV_NT, 0, s>>>(g, dim, o, orig_id, cell_start,
+                                                                             big_list, big_count);
+        k_sort_convert_big<SPH_PREC_FP64_CLL><<<sm_count, SORTCV_NT, 0, s>>>(g, dim, o, orig_id, cell_start,
+                                                                             big_list, big_count);
+    }
     return cudaGetLastError();
 }
 
