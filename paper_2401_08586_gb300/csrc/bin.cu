@@ -58,11 +58,14 @@ __global__ void k_bounds(const double *__restrict__ xyz, long long total, int di
     const bool aligned = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
     const long long nchunk = aligned ? total / 6 : 0;
     const ulonglong2 *v2 = reinterpret_cast<const ulonglong2 *>(xyz);
-    for (long long c = t; c < nchunk; c += stride) {
+    // two chunks per iteration: six 16-byte loads in flight per thread
+    for (long long c = t; c < nchunk; c += 2 * stride) {
+        const long long c2 = c + stride < nchunk ? c + stride : c;  // repeats c at the end (min/max are idempotent)
         const ulonglong2 a = __ldg(v2 + 3 * c), b = __ldg(v2 + 3 * c + 1), d = __ldg(v2 + 3 * c + 2);
-        const unsigned long long e[6] = {a.x, a.y, b.x, b.y, d.x, d.y};
+        const ulonglong2 a2 = __ldg(v2 + 3 * c2), b2 = __ldg(v2 + 3 * c2 + 1), d2 = __ldg(v2 + 3 * c2 + 2);
+        const unsigned long long e[12] = {a.x, a.y, b.x, b.y, d.x, d.y, a2.x, a2.y, b2.x, b2.y, d2.x, d2.y};
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
+        for (int j = 0; j < 12; ++j) {
             const int ax = j % 3;
             if (dim == 3) key_minmax(e[j], mn[ax], mx[ax], bad);
             else key_minmax(e[j], mn[j & 1], mx[j & 1], bad);
@@ -274,7 +277,9 @@ cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st
     const int nt = 256;
     ProfScope ps(TAG_BOUNDS, s);
     note_launch(1);
-    k_bounds<<<grid_for((n * dim + 5) / 6, nt, sm_count, 8), nt, 0, s>>>(xyz, n * dim, dim, st);
+    // few blocks, each thread over several chunks: the block reduction and
+    // the per-block atomics on the six bounds stay a small part
+    k_bounds<<<grid_for((n * dim + 5) / 6, nt, sm_count, 2), nt, 0, s>>>(xyz, n * dim, dim, st);
     return cudaGetLastError();
 }
 
