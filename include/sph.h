@@ -270,8 +270,8 @@ int sph_grid_export(sph_grid_t grid, int32_t *orig_id, int32_t *rank, int32_t *c
 
 /* Copy the stored cell-relative coordinates (Eq. 6, SPH_PREC_FP16_RCLL grids
  * only) in sorted order into caller buffers (device memory, either may be
- * NULL): rel16 uint16[n][4] (FP16 bit patterns x, y, z, 0), rel32 float[n][4]
- * (x, y, z, 0).  Units u = h_c / 2 relative to the centre of the particle's
+ * NULL): rel16 uint16[n][4] (FP16 bit patterns of x, y, z, then the cell x
+ * index modulo 2^16 as an unsigned integer), rel32 float[n][4] (x, y, z, 0).  Units u = h_c / 2 relative to the centre of the particle's
  * cell: for s = 2 (x - lo) / h_c rounded to FP64 (one fused multiply-add
  * when every coordinate lies within 2^17 u of the origin, else a subtraction
  * and a multiplication) and c = min(floor(s / 2), n_k - 1), the FP32 value is

@@ -76,7 +76,7 @@ __global__ void k_advance(GridDev g, const int *__restrict__ scell, const double
             rel64u[i] = make_double4(a[0], a[1], a[2], 0.0);
             uint2 q;
             float4 f;
-            round_rel(a, q, f);
+            round_rel(a, cc[0], q, f);
             rel16u[i] = q;
             rel32u[i] = f;
         }

@@ -127,7 +127,7 @@ __global__ void k_batch_hash(const BinSys *__restrict__ sys, const long long *__
             c = S.cell_base + (cc[2] * S.nk[1] + cc[1]) * S.nk[0] + cc[0];
             uint2 q;
             float4 f;
-            round_rel_f(fr[0], fr[1], fr[2], q, f);
+            round_rel_f(fr[0], fr[1], fr[2], cc[0], q, f);
             rel16u[I] = q;
             rel32u[I] = f;
         }

@@ -143,7 +143,7 @@ __global__ void k_hash(const double *__restrict__ xyz, int n, GridDev g,
             if (PREC == SPH_PREC_FP16_RCLL) {
                 uint2 q;
                 float4 f;
-                round_rel_f(fr[0], fr[1], fr[2], q, f);
+                round_rel_f(fr[0], fr[1], fr[2], cc[0], q, f);
                 rel16u[i] = q;
                 rel32u[i] = f;
             }

@@ -198,7 +198,7 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
     int kept = 0;
     while (cur < total && kept + 32 <= C::CMAX) {
         const int nu = kept + 32 * U <= C::CMAX ? U : 1;  // warp-uniform
-        int jk[U], rr[U], cx[U];
+        int jk[U], rr[U];
         bool valid[U];
         uint2 q[U];
 #pragma unroll
@@ -211,13 +211,12 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
             rr[u] = r;
             jk[u] = k + S.rt[r].x;
             q[u] = valid[u] ? g.rel16[jk[u]] : make_uint2(0u, 0u);
-            cx[u] = valid[u] ? g.scell_x[jk[u]] : G.xm;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (u >= nu) break;
             const int4 rt = S.rt[rr[u]];
-            const int ox = cx[u] - G.xm;  // frame cell offset in x, |ox| <= 3
+            const int ox = rel_cell_offset(q[u], G.xm);  // frame cell offset in x, |ox| <= 3
             bool keep = false;
             if (valid[u]) {
                 const float2 xy = __half22float2(as_h2(q[u].x));

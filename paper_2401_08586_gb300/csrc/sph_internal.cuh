@@ -169,16 +169,23 @@ __device__ __forceinline__ bool rel_axis_bits(double s, int nk, int &c, float &f
 // The stored relative coordinates: FP32 rounded once from the FP64 value,
 // FP16 rounded from the FP32 value.  The second rounding adds at most 2^-25
 // u to the FP16 coordinate's error (2^-12 u for |x_rel| <= 1), far inside the
-// FP16 band's margin.
-__device__ __forceinline__ void round_rel_f(float f0, float f1, float f2, uint2 &q16, float4 &f32) {
+// FP16 band's margin.  The FP16 record is x, y, z and the particle's cell x
+// modulo 2^16 (an unsigned 16-bit integer): the tile search's candidates lie
+// within 3 cells of their group's middle cell, so the 16-bit difference
+// gives their cell offset exactly with the coordinates' one load.
+__device__ __forceinline__ void round_rel_f(float f0, float f1, float f2, int cx, uint2 &q16, float4 &f32) {
     const __half2 xy = __floats2half2_rn(f0, f1);
-    const __half2 z0 = __floats2half2_rn(f2, 0.f);
+    const __half z = __float2half_rn(f2);
     q16.x = *reinterpret_cast<const unsigned int *>(&xy);
-    q16.y = *reinterpret_cast<const unsigned int *>(&z0);
+    q16.y = (unsigned int)*reinterpret_cast<const unsigned short *>(&z) | ((unsigned int)cx << 16);
     f32 = make_float4(f0, f1, f2, 0.f);
 }
-__device__ __forceinline__ void round_rel(const double a[3], uint2 &q16, float4 &f32) {
-    round_rel_f(__double2float_rn(a[0]), __double2float_rn(a[1]), __double2float_rn(a[2]), q16, f32);
+__device__ __forceinline__ void round_rel(const double a[3], int cx, uint2 &q16, float4 &f32) {
+    round_rel_f(__double2float_rn(a[0]), __double2float_rn(a[1]), __double2float_rn(a[2]), cx, q16, f32);
+}
+// Cell offset (-3 .. 3) of a candidate's FP16 record from cell x `xm`.
+__device__ __forceinline__ int rel_cell_offset(uint2 q16, int xm) {
+    return (int)(short)(unsigned short)((q16.y >> 16) - (unsigned int)xm);
 }
 
 // Row tiles of the single-pass search: runs of at most TILE_ROWS

@@ -653,8 +653,9 @@ class Grid:
         return out
 
     def relative_coordinates(self, stream=None):
-        """(rel16, rel32) in sorted order: float16[N, 4] and float32[N, 4]
-        tensors of the stored cell-relative coordinates (x, y, z, 0)."""
+        """(rel16, rel32) in sorted order: float16[N, 4] (x, y, z, then the
+        bits of the cell x index modulo 2^16) and float32[N, 4] (x, y, z, 0)
+        tensors of the stored cell-relative coordinates."""
         import torch
         r16 = torch.empty((self.n, 4), dtype=torch.int16, device=self.xyz.device)
         r32 = torch.empty((self.n, 4), dtype=torch.float32, device=self.xyz.device)

@@ -2,7 +2,8 @@
 definition, evaluated here on the CPU: s = 2 (x - lo) / h_c rounded to FP64
 (one fused multiply-add s = RN(x t + b) with t = RN(2 / h_c), b = RN(-lo t)
 when every coordinate lies within 2^17 u of the origin, else RN(RN(x - lo) t)),
-c = min(floor(s / 2), n_k - 1), FP32 = RN32(s - (2c + 1)), FP16 = RN16(FP32).
+c = min(floor(s / 2), n_k - 1), FP32 = RN32(s - (2c + 1)), FP16 = RN16(FP32);
+the FP16 record's fourth entry is the cell x modulo 2^16.
 The fused multiply-add is evaluated exactly with rationals and rounded once
 (Python's float(Fraction) rounds to nearest).  Covers the particle at the
 lower bound (s = 0), the half cell next to it (s < 1), the upper clamp, and a
@@ -37,6 +38,7 @@ def reference(xyz, kh):
     nk = [max(1, int(math.ceil((hi[k] - lo[k]) / hc))) for k in range(dim)]
     fma = all(max(abs(lo[k]), abs(lo[k] + nk[k] * hc)) * t <= 131072.0 for k in range(dim))
     f32 = np.zeros((n, 4), dtype=np.float32)
+    cx = None
     for k in range(dim):
         b = -lo[k] * t
         if fma:
@@ -46,9 +48,13 @@ def reference(xyz, kh):
             s = (xyz[:, k] - lo[k]) * t
         c = np.minimum(np.floor(s).astype(np.int64) >> 1, nk[k] - 1)
         c = np.maximum(c, 0)
+        if k == 0:
+            cx = c
         a = s - (2 * c + 1).astype(np.float64)
         f32[:, k] = a.astype(np.float32)
-    return f32, f32.astype(np.float16), fma
+    f16 = f32.astype(np.float16).view(np.uint16).copy()
+    f16[:, 3] = (cx & 0xFFFF).astype(np.uint16)
+    return f32, f16, fma
 
 
 def check(sph, xyz, h, expect_fma):
@@ -62,7 +68,7 @@ def check(sph, xyz, h, expect_fma):
     got32 = r32.cpu().numpy().view(np.uint32)
     got16 = r16.cpu().numpy().view(np.uint16)
     want32 = f32[orig].view(np.uint32)
-    want16 = f16[orig].view(np.uint16)
+    want16 = f16[orig]
     bad = np.nonzero((got32 != want32).any(axis=1))[0]
     assert bad.size == 0, (bad[:5], got32[bad[:5]], want32[bad[:5]])
     assert np.array_equal(got16, want16)
