@@ -87,9 +87,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_name, kernel_tag):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+def ncu_traffic(workload_name, kernel_tag, key="bytes_per_launch"):
+    """DRAM bytes (or, key="inst_per_launch", warp instructions) per launch of
+    the dominant kernel from the committed ncu summary, only if it was taken
+    on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -97,9 +98,14 @@ def ncu_traffic(workload_name, kernel_tag):
         e = d[workload_name][kernel_tag]
         if e.get("source_hash") != kernel_source_hash():
             return None
-        return float(e["bytes_per_launch"])
+        return float(e[key])
     except Exception:
         return None
+
+
+# Instruction issue of GB300: 152 SMs x 4 schedulers, one warp instruction
+# per scheduler per clock.
+ISSUE_PER_CLOCK = 152 * 4
 
 
 class ClockSampler:
@@ -372,7 +378,27 @@ def main():
     roofline = {"bound": "hbm", "kernel": "k_nnps_tile" if dom == "fused" else "k_nnps<fill>",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "launch_ms": dom_ms, "algorithmic_bytes_per_launch": alg_dom,
-                "traffic": ncu_traffic(args.workload, dom)}
+                "traffic": None}
+    # the committed figures are per launch over 1,000,000 particles (the
+    # recipe at side 100); other sides scale with the particle count
+    per_m = n / 1.0e6
+    traffic = ncu_traffic(args.workload, dom)
+    if traffic is not None:
+        roofline["traffic"] = traffic * per_m
+    # the bound that applies to the search: instruction issue (measured warp
+    # instructions per launch from the committed capture, scaled to this
+    # workload, over the event-timed launch, against the issue rate at the SM
+    # clock sampled during the timed region)
+    clocks = clk.summary()
+    inst = ncu_traffic(args.workload, dom, "inst_per_launch")
+    inst = None if inst is None else inst * per_m
+    issue = None
+    if inst is not None and clocks.get("sm_mhz"):
+        ipeak = ISSUE_PER_CLOCK * clocks["sm_mhz"] * 1e6
+        ia = inst / (dom_ms * 1e-3)
+        issue = {"bound": "issue", "kernel": roofline["kernel"], "achieved": ia, "peak": ipeak,
+                 "unit": "warp-instructions/s", "frac": ia / ipeak, "inst_per_launch": inst,
+                 "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction/clock x sampled SM clock"}
     # whole path: binning 56 B/particle, search + fused density 36 B/particle + 4 B/neighbour
     alg_step = n * (56 + 36) + 4 * nnz
     step_ms_mean = 1e3 * dev_total_s / args.steps
@@ -383,9 +409,10 @@ def main():
         "config": {"workload": desc, "n_particles": n, "dim": ps.dim, "order": "cell",
                    "density": "fused, fp32 accumulation", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "gpu_launches": launches,
         "roofline": roofline,
+        "roofline_issue": issue,
         "nnz": nnz, "neighbours_per_particle": nnz / n,
         "step_hbm_frac": alg_step / (step_ms_mean * 1e-3) / 1e9 / peak,
         "step_algorithmic_bytes": alg_step,
