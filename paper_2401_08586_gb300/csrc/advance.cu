@@ -23,7 +23,7 @@ __device__ __forceinline__ void cell_xyz(const GridDev &g, int c, int cc[3]) {
 // rel64[s] from the positions, each particle in its current cell:
 // s_k = 2 (x_k - lo_k) / h_c, a_k = s_k - (2 c_k + 1) (the binning formula).
 __global__ void k_rel64_sync(GridDev g, const int *__restrict__ scell, const double *__restrict__ xyz,
-                             double4 *__restrict__ rel64) {
+                             double4_32a *__restrict__ rel64) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n;
          s += (long long)gridDim.x * blockDim.x) {
         const int i = g.orig_id[s];
@@ -34,17 +34,17 @@ __global__ void k_rel64_sync(GridDev g, const int *__restrict__ scell, const dou
             const double sk = __dmul_rn(__dsub_rn(xyz[(long long)i * g.dim + k], g.lo[k]), g.two_over_hc);
             a[k] = __dsub_rn(sk, (double)(2 * cc[k] + 1));
         }
-        rel64[s] = make_double4(a[0], a[1], a[2], 0.0);
+        rel64[s] = make_double4_32a(a[0], a[1], a[2], 0.0);
     }
 }
 
 // Eq. 8 with the displacement of Eq. 9 for every sorted particle, its new
 // cell, the warp-aggregated histogram of the new cells, and the rounded
 // relative coordinates, all in input order for the gather of the re-sort.
-__global__ void k_advance(GridDev g, const int *__restrict__ scell, const double4 *__restrict__ rel64,
+__global__ void k_advance(GridDev g, const int *__restrict__ scell, const double4_32a *__restrict__ rel64,
                           const double *__restrict__ vel, double dt, int *__restrict__ cnt, int *__restrict__ cid,
                           int *__restrict__ slot, uint2 *__restrict__ rel16u, float4 *__restrict__ rel32u,
-                          double4 *__restrict__ rel64u) {
+                          double4_32a *__restrict__ rel64u) {
     const int lane = threadIdx.x & 31;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < g.n; base += (long long)gridDim.x * blockDim.x) {
         const long long s = base + threadIdx.x;
@@ -56,7 +56,7 @@ __global__ void k_advance(GridDev g, const int *__restrict__ scell, const double
             i = g.orig_id[s];
             int cc[3];
             cell_xyz(g, scell[s], cc);
-            const double4 r = rel64[s];
+            const double4_32a r = rel64[s];
             double a[3] = {r.x, r.y, r.z};
             for (int k = 0; k < g.dim; ++k) {
                 const double d = __dmul_rn(vel[(long long)i * g.dim + k], dt);  // Eq. 9
@@ -73,7 +73,7 @@ __global__ void k_advance(GridDev g, const int *__restrict__ scell, const double
                 cc[k] = (int)(ck < 0 ? 0 : (ck >= g.nk[k] ? g.nk[k] - 1 : ck));
             }
             c = (cc[2] * g.nk[1] + cc[1]) * g.nk[0] + cc[0];
-            rel64u[i] = make_double4(a[0], a[1], a[2], 0.0);
+            rel64u[i] = make_double4_32a(a[0], a[1], a[2], 0.0);
             uint2 q;
             float4 f;
             round_rel(a, cc[0], q, f);
@@ -108,7 +108,7 @@ unsigned grid_blocks(long long n, int nt, int sm_count) {
 
 }  // namespace
 
-cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *xyz, double4 *rel64, int sm_count,
+cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *xyz, double4_32a *rel64, int sm_count,
                               cudaStream_t s) {
     ProfScope ps(TAG_CONVERT, s);
     note_launch(1);
@@ -116,8 +116,8 @@ cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_advance(const GridDev &g, const int *scell, const double4 *rel64, const double *vel, double dt,
-                           int *cnt, int *cid, int *slot, uint2 *rel16u, float4 *rel32u, double4 *rel64u,
+cudaError_t launch_advance(const GridDev &g, const int *scell, const double4_32a *rel64, const double *vel, double dt,
+                           int *cnt, int *cid, int *slot, uint2 *rel16u, float4 *rel32u, double4_32a *rel64u,
                            int sm_count, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(cnt, 0, cnt_bytes(g.ncell), s);  // counters and their scan state
     if (e != cudaSuccess) return e;

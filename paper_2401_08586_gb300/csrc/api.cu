@@ -191,7 +191,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
                 (rc = ensure(g->rel16u, nn * sizeof(uint2), s)) || (rc = ensure(g->rel32u, nn * sizeof(float4), s)))
                 break;
         } else {
-            if ((rc = ensure(g->x64, nn * sizeof(double4), s))) break;
+            if ((rc = ensure(g->x64, nn * sizeof(double4_32a), s))) break;
         }
         if (n == 0) {
             if (cudaMemsetAsync(g->cell_start.p, 0, (ncell + 1) * sizeof(int), s) != cudaSuccess) {
@@ -204,7 +204,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
         cudaError_t e = launch_hash_scatter_convert(
             d, xyz, (int)n, dim, p->precision, P<int>(g->cnt), P<int>(g->cid), P<int>(g->slot),
             P<int>(g->cell_start), P<int>(g->orig_id), P<int>(g->rank), P<int>(g->scell), P<uint2>(g->rel16),
-            P<float4>(g->rel32), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4>(g->x64), P<int>(g->scell_x),
+            P<float4>(g->rel32), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4_32a>(g->x64), P<int>(g->scell_x),
             g->scan_tmp.p, P<int>(g->big_list),
             &P<DevStatus>(g->status)->big_cells, p->have_box, g->sm_count, s);
         if (e != cudaSuccess) {
@@ -233,18 +233,18 @@ extern "C" int sph_advance(sph_grid_t grid, const double *xyz_new, const double 
     cudaStream_t s = (cudaStream_t)stream;
     g->stream = s;
     if (g->p.precision != SPH_PREC_FP16_RCLL || n == 0) return sph_bin_cells(&g->p, xyz_new, n, stream, &grid);
-    SPH_TRY(ensure(g->rel64, (size_t)n * sizeof(double4), s));
-    SPH_TRY(ensure(g->rel64u, (size_t)n * sizeof(double4), s));
+    SPH_TRY(ensure(g->rel64, (size_t)n * sizeof(double4_32a), s));
+    SPH_TRY(ensure(g->rel64u, (size_t)n * sizeof(double4_32a), s));
     GridDev d = make_dev(g);
     if (!g->rel64_valid || g->drift > DRIFT_BUDGET) {
         // derive the FP64 relative coordinates from the current positions
-        SPH_CUDA(launch_rel64_sync(d, P<int>(g->scell), g->xyz, P<double4>(g->rel64), g->sm_count, s));
+        SPH_CUDA(launch_rel64_sync(d, P<int>(g->scell), g->xyz, P<double4_32a>(g->rel64), g->sm_count, s));
         g->rel64_valid = true;
         g->drift = 0;
     }
     SPH_CUDA(launch_status_init(P<DevStatus>(g->status), s));
-    SPH_CUDA(launch_advance(d, P<int>(g->scell), P<double4>(g->rel64), vel, dt, P<int>(g->cnt), P<int>(g->cid),
-                            P<int>(g->slot), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4>(g->rel64u),
+    SPH_CUDA(launch_advance(d, P<int>(g->scell), P<double4_32a>(g->rel64), vel, dt, P<int>(g->cnt), P<int>(g->cid),
+                            P<int>(g->slot), P<uint2>(g->rel16u), P<float4>(g->rel32u), P<double4_32a>(g->rel64u),
                             g->sm_count, s));
     SPH_TRY(read_status(g));
     if (g->h_status->flags & ST_NONFINITE) return fail(SPH_ERR_INVALID, "non-finite velocity or displacement");
@@ -270,7 +270,7 @@ extern "C" int sph_advance(sph_grid_t grid, const double *xyz_new, const double 
     SPH_CUDA(launch_order_convert(d, (int)n, g->p.dim, SPH_PREC_FP16_RCLL, P<int>(g->cnt), P<int>(g->cid),
                                   P<int>(g->slot), P<int>(g->cell_start), P<int>(g->orig_id), P<int>(g->rank),
                                   P<int>(g->scell), P<uint2>(g->rel16), P<float4>(g->rel32), P<uint2>(g->rel16u),
-                                  P<float4>(g->rel32u), P<double4>(g->rel64u), P<double4>(g->rel64), nullptr,
+                                  P<float4>(g->rel32u), P<double4_32a>(g->rel64u), P<double4_32a>(g->rel64), nullptr,
                                   P<int>(g->scell_x),
                                   g->scan_tmp.p, P<int>(g->big_list), &P<DevStatus>(g->status)->big_cells,
                                   g->sm_count, s));

@@ -177,8 +177,8 @@ struct ConvertOut {
     float4 *rel32;
     const uint2 *rel16u;
     const float4 *rel32u;
-    const double4 *rel64u;
-    double4 *rel64, *x64;
+    const double4_32a *rel64u;
+    double4_32a *rel64, *x64;
 };
 
 template <int PREC>
@@ -190,7 +190,7 @@ __device__ __forceinline__ void convert_pos(const GridDev &g, int dim, const Con
     if (PREC == SPH_PREC_FP64_CLL) {
         double x[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < dim; ++k) x[k] = g.xyz[(long long)i * dim + k];
-        o.x64[s] = make_double4(x[0], x[1], x[2], 0.0);
+        o.x64[s] = make_double4_32a(x[0], x[1], x[2], 0.0);
     } else {
         o.rel16[s] = o.rel16u[i];
         o.rel32[s] = o.rel32u[i];
@@ -285,8 +285,8 @@ cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st
 
 cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
                                  int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
-                                 const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,
-                                 double4 *x64, int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
+                                 const uint2 *rel16u, const float4 *rel32u, const double4_32a *rel64u, double4_32a *rel64,
+                                 double4_32a *x64, int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
                                  int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);
@@ -327,7 +327,7 @@ cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec,
                                         int *cnt, int *cid, int *slot, int *cell_start, int *orig_id,
                                         int *rank, int *scell, uint2 *rel16, float4 *rel32, uint2 *rel16u,
-                                        float4 *rel32u, double4 *x64, int *scell_x, void *scan_tmp, int *big_list,
+                                        float4 *rel32u, double4_32a *x64, int *scell_x, void *scan_tmp, int *big_list,
                                         unsigned int *big_count, int check_box, int sm_count, cudaStream_t s) {
     const int nt = 256;
     const unsigned blocks = grid_for(n, nt, sm_count, 16);

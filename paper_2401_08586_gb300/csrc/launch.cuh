@@ -12,7 +12,7 @@ namespace sph {
 cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count, cudaStream_t s);
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec, int *cnt,
                                         int *cid, int *slot, int *cell_start, int *orig_id, int *rank, int *scell,
-                                        uint2 *rel16, float4 *rel32, uint2 *rel16u, float4 *rel32u, double4 *x64,
+                                        uint2 *rel16, float4 *rel32, uint2 *rel16u, float4 *rel32u, double4_32a *x64,
                                         int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
                                         int check_box, int sm_count, cudaStream_t s);
 // Scan of the cell histogram, scatter, per-cell sort and the gather of the
@@ -22,8 +22,8 @@ cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int
 // histogram was counted.
 cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int *cnt, int *cid, int *slot,
                                  int *cell_start, int *orig_id, int *rank, int *scell, uint2 *rel16, float4 *rel32,
-                                 const uint2 *rel16u, const float4 *rel32u, const double4 *rel64u, double4 *rel64,
-                                 double4 *x64, int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
+                                 const uint2 *rel16u, const float4 *rel32u, const double4_32a *rel64u, double4_32a *rel64,
+                                 double4_32a *x64, int *scell_x, void *scan_tmp, int *big_list, unsigned int *big_count,
                                  int sm_count, cudaStream_t s);
 cudaError_t launch_scatter(int n, const int *cell_start, const int *cid, const int *slot, int *orig_id,
                            int sm_count, cudaStream_t s);
@@ -33,12 +33,12 @@ cudaError_t launch_scatter(int n, const int *cell_start, const int *cid, const i
 // [-1, 1]; input-order outputs (cid, slot with the histogram cnt, rel16u,
 // rel32u, rel64u) ready for launch_order_convert.  Status: ST_OUT_OF_BOX when
 // a particle leaves the grid, max |v dt| as a key in max_key[0].
-cudaError_t launch_advance(const GridDev &g, const int *scell, const double4 *rel64, const double *vel, double dt,
-                           int *cnt, int *cid, int *slot, uint2 *rel16u, float4 *rel32u, double4 *rel64u,
+cudaError_t launch_advance(const GridDev &g, const int *scell, const double4_32a *rel64, const double *vel, double dt,
+                           int *cnt, int *cid, int *slot, uint2 *rel16u, float4 *rel32u, double4_32a *rel64u,
                            int sm_count, cudaStream_t s);
 // FP64 relative coordinates of the sorted particles from positions xyz in
 // their current cells (the conversion of binning, cells unchanged).
-cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *xyz, double4 *rel64, int sm_count,
+cudaError_t launch_rel64_sync(const GridDev &g, const int *scell, const double *xyz, double4_32a *rel64, int sm_count,
                               cudaStream_t s);
 
 // Two-pass search, unfused density, canonical order (search.cu).

@@ -65,7 +65,7 @@ struct SmemGen<SPH_PREC_FP16_RCLL> : SmemGenBase {
 template <>
 struct SmemGen<SPH_PREC_FP64_CLL> : SmemGenBase {
     double cx[CAPC], cy[CAPC], cz[CAPC];
-    double4 h64[HB];
+    double4_32a h64[HB];
     double racc[HB];
     double pw[PAIRCAP];
 };
@@ -306,7 +306,7 @@ __device__ void cell_general(SmemGen<PREC> &S, const GridDev &g, long long cell,
                 S.h32[tid] = g.rel32[i];
                 S.racc[tid] = g.w_self;
             } else {
-                S.h64[tid] = reinterpret_cast<const double4 *>(g.x64)[i];
+                S.h64[tid] = reinterpret_cast<const double4_32a *>(g.x64)[i];
                 S.racc[tid] = g.w_self64;
             }
         }
@@ -336,7 +336,7 @@ __device__ void cell_general(SmemGen<PREC> &S, const GridDev &g, long long cell,
                         reinterpret_cast<__half *>(S.hy)[2 * w + hi] = __high2half(xy);
                         reinterpret_cast<__half *>(S.hz)[2 * w + hi] = zz;
                     } else {
-                        double4 x = reinterpret_cast<const double4 *>(g.x64)[j];
+                        double4_32a x = reinterpret_cast<const double4_32a *>(g.x64)[j];
                         S.cx[p] = x.x;
                         S.cy[p] = x.y;
                         S.cz[p] = x.z;
@@ -374,7 +374,7 @@ __device__ void cell_general(SmemGen<PREC> &S, const GridDev &g, long long cell,
                     const double xb[3] = {S.cx[pb], S.cy[pb], S.cz[pb]};
                     const int ja = S.cand_j[pa], jb = S.cand_j[pb];
                     for (int k = 0; k < nb; ++k) {
-                        const double4 h = S.h64[k];
+                        const double4_32a h = S.h64[k];
                         const double xi[3] = {h.x, h.y, h.z};
                         const int i = S.hid[k];
                         const bool ina = ja != i && r2_fp64(DIM, xi, xa) < g.kh2;
@@ -456,7 +456,7 @@ __device__ void cell_general(SmemGen<PREC> &S, const GridDev &g, long long cell,
                     } else {
                         in = 1;  // the test was already the exact FP64 one
                         if (want_rho) {
-                            const double4 h = S.h64[k];
+                            const double4_32a h = S.h64[k];
                             const double xi[3] = {h.x, h.y, h.z};
                             const double xj[3] = {S.cx[p], S.cy[p], S.cz[p]};
                             w = g.w_norm64 * w_poly64(sqrt(r2_fp64(DIM, xi, xj)) * g.r_scale64);

@@ -63,12 +63,12 @@ __global__ void k_density(GridDev g, const int *__restrict__ rank, const int *__
             }
             rho[r] = acc;
         } else {
-            const double4 h = reinterpret_cast<const double4 *>(g.x64)[si];
+            const double4_32a h = reinterpret_cast<const double4_32a *>(g.x64)[si];
             const double xi[3] = {h.x, h.y, h.z};
             double acc = g.w_self64;
             for (long long q = row_ptr[r]; q < row_ptr[r + 1]; ++q) {
                 const int sj = canonical ? rank[col[q]] : col[q];
-                const double4 x = reinterpret_cast<const double4 *>(g.x64)[sj];
+                const double4_32a x = reinterpret_cast<const double4_32a *>(g.x64)[sj];
                 const double xj[3] = {x.x, x.y, x.z};
                 acc += g.w_norm64 * w_poly64(sqrt(r2_fp64(DIM, xi, xj)) * g.r_scale64);
             }
