@@ -54,24 +54,26 @@ constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch ma
 // Shared-memory shape of the tile search: kept candidates per pass (the
 // bitmask length), per staging window, warps per CTA and the resident warps
 // per SM it is built for (the register budget: 96 per thread at 20 warps,
-// 128 at 16).  Each warp works alone on its own tiles in its own
+// 128 at 16), and the walk's bits in flight per lane (measured: 3 at 20
+// warps, 4 at 16).  Each warp works alone on its own tiles in its own
 // shared-memory area; two warps per CTA share the SM's per-CTA reservation.
 // Sparse: 10.8 KB per warp, 20 warps per SM; its output area (code, pw and
 // f32 after the last window) holds 2,640 entries, a tile of 32 rows of up to
 // ~80 neighbours.  Dense: 13.7 KB, 16 warps, 832 kept candidates and 3,488
 // output entries for denser particle sets.
-template <int CMAX_, int WIN_, int WPB_, int WSM_>
+template <int CMAX_, int WIN_, int WPB_, int WSM_, int WB_>
 struct TileCfg {
     static constexpr int CMAX = CMAX_;
     static constexpr int WIN = WIN_;
     static constexpr int WPB = WPB_;
     static constexpr int WSM = WSM_;
+    static constexpr int WB = WB_;  // bits in flight per lane in the walk (independent loads and arithmetic)
     static constexpr int NWORD = CMAX_ / 32;
     static_assert(CMAX_ % 32 == 0 && WIN_ % 32 == 0 && WIN_ <= CMAX_, "tile shape");
     static_assert(WSM_ % WPB_ == 0, "warps per CTA");
 };
-using TileSparse = TileCfg<672, 192, 2, 20>;
-using TileDense = TileCfg<832, 256, 2, 16>;
+using TileSparse = TileCfg<672, 192, 2, 20, 3>;
+using TileDense = TileCfg<832, 256, 2, 16, 4>;
 
 
 template <class C>
@@ -339,7 +341,6 @@ __device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, int wb
     }
 }
 
-constexpr int WALK_BATCH = 4;  // bits in flight per lane (independent loads and arithmetic)
 
 // The FP64 definition for the rare pairs inside the FP32 band.  Kept out of
 // line so that its global loads and FP64 arithmetic are never hoisted into
@@ -362,16 +363,16 @@ __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, co
     int gi = 0;
     unsigned int w = 0u;
     while (true) {
-        int p[WALK_BATCH];
-        bool v[WALK_BATCH];
-        next_bits<WALK_BATCH, C>(S, lane, wbase, nem, gi, w, p, v);
+        int p[C::WB];
+        bool v[C::WB];
+        next_bits<C::WB, C>(S, lane, wbase, nem, gi, w, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
-        float r2[WALK_BATCH];
-        int jj[WALK_BATCH];
-        bool in[WALK_BATCH];
+        float r2[C::WB];
+        int jj[C::WB];
+        bool in[C::WB];
         bool odd = false;
 #pragma unroll
-        for (int k = 0; k < WALK_BATCH; ++k) {
+        for (int k = 0; k < C::WB; ++k) {
             const float4 c = S.f32[v[k] ? p[k] : 0];
             jj[k] = __float_as_int(c.w);
             const float d0 = __fsub_rn(c.x, h.x32);
@@ -383,7 +384,7 @@ __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, co
         }
         if (__any_sync(0xffffffffu, odd)) {
 #pragma unroll
-            for (int k = 0; k < WALK_BATCH; ++k) {
+            for (int k = 0; k < C::WB; ++k) {
                 if (v[k] && !in[k]) {
                     if (r2[k] <= g.t32_out) {
                         ++n64;
@@ -397,11 +398,11 @@ __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, co
         }
         if (PASS == PASS_EMIT) {
 #pragma unroll
-            for (int k = 0; k < WALK_BATCH; ++k)
+            for (int k = 0; k < C::WB; ++k)
                 if (in[k]) col[rp + cnt++] = jj[k];
         } else {
 #pragma unroll
-            for (int k = 0; k < WALK_BATCH; ++k) {
+            for (int k = 0; k < C::WB; ++k) {
                 const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
                 acc += in[k] ? wk : 0.f;
             }
