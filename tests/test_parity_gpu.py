@@ -294,3 +294,16 @@ def test_tile_shapes_and_staging(sph, case, shape, staging):
     rp, col, rho = g.query()
     out = dict(rp=rp.cpu().numpy(), col=col.cpu().numpy(), rho=rho.cpu().numpy(), orig=g.orig_id().cpu().numpy())
     check_against_oracle(out, xyz, h, 2 * h, 0)
+
+
+@pytest.mark.parametrize("dim,n,h", [(3, 200000, 0.0025), (2, 300000, 0.0001)])
+def test_large_sparse_grid(sph, dim, n, h):
+    """A sparse set over a fine grid (8M cells in 3D, 25M in 2D): the
+    one-launch cell scan has more tiles of 4096 cells, and the one-launch
+    tile-list builder more chunks of rows, than blocks, so blocks take several
+    of them in ticket order."""
+    xyz = W.random_uniform(n, dim, 31 + dim)
+    out = run(sph, xyz, h, 2 * h, 0)
+    info = out["info"]
+    assert info.ncell > 152 * 4 * 4096
+    check_against_oracle(out, xyz, h, 2 * h, 0)
