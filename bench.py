@@ -81,7 +81,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("nnps_tile.cu", "nnps_common.cuh", "sph_internal.cuh"):
+    for name in ("nnps_tile.cu", "nnps_common.cuh", "sph_internal.cuh", "lookback.cuh", "fastdiv.h"):
         with open(os.path.join(ROOT, "paper_2401_08586_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
