@@ -430,6 +430,7 @@ def main():
                                                                                     dev)
         line["e2e"].pop("seconds", None)
         line["gradient_a5"] = bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, args.steps)
+        line["density_half"] = bench_density_half(sph, ps, grid, dev, stream, args.steps)
         line["timestep"] = bench_timestep(sph, ps, xyz, dev, stream, row_ptr, col, cap, rho, args.steps)
         line["serving"] = bench_serve(sph, dev, count=450, warm=50)
         if world == 1 and rank == 0:
@@ -495,6 +496,28 @@ def bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, steps):
             ms.append(a.elapsed_time(b))
     t = sum(ms) / len(ms)
     return {"ms": t, "particles_per_s": ps.n / (t * 1e-3), "field": "x^3"}
+
+
+def bench_density_half(sph, ps, grid, dev, stream, steps):
+    """The summation density over the half stencil (no neighbour list) on
+    the step's grid, CUDA events on the stream, L2 flushed between calls."""
+    import torch
+    rho = torch.empty(ps.n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sptr = stream.cuda_stream
+    ms = []
+    for k in range(steps + 3):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sph.sph_density_half(grid, rho, sptr)
+        b.record(stream)
+        b.synchronize()
+        if k >= 3:
+            ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    return {"ms": t, "particles_per_s": ps.n / (t * 1e-3),
+            "note": "density only (no CSR); the search with CSR and fused density is roofline.launch_ms"}
 
 
 def bench_timestep(sph, ps, xyz, dev, stream, row_ptr, col, cap, rho, steps):

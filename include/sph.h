@@ -163,6 +163,20 @@ int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col,
                     void *stream);
 
 /*
+ * SPH summation density without a neighbour list, over a half stencil:
+ * rho_i = m W(0, h) + sum_{j in N(i)} m W(r_ij / h, h) (Eq. 3), each pair
+ * tested once and its weight added to both particles -- the reuse of
+ * computed distances raised in the paper's conclusions.  The pairs are
+ * decided exactly as by sph_nnps_query (FP32 with the FP64 definition inside
+ * the band); weights in FP32.  The partner's share is added atomically, so
+ * the order of the FP32 additions varies between calls (results agree to
+ * ~1e-7 relative).  rho: device float[n], indexed by sorted position (row r
+ * is input particle orig_id[r]).  FP16-RCLL grids in cell order only
+ * (SPH_ERR_INVALID otherwise).  Enqueued on `stream`.
+ */
+int sph_density_half(sph_grid_t grid, float *rho, void *stream);
+
+/*
  * Volume-free normalised first-order gradient of a particle field f
  * (Appendix Eq. A5): for each axis a,
  *   grad_a f_i = sum_j (f_j - f_i) dW_ij/dx^a / sum_j (x_j^a - x_i^a) dW_ij/dx^a

@@ -396,6 +396,21 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
     return status_to_code(g->h_status->flags);
 }
 
+extern "C" int sph_density_half(sph_grid_t grid, float *rho, void *stream) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (g->p.precision != SPH_PREC_FP16_RCLL) return fail(SPH_ERR_INVALID, "FP16-RCLL grids only");
+    if (g->p.order != SPH_ORDER_CELL) return fail(SPH_ERR_INVALID, "cell-order grids only");
+    if (g->n > 0 && !rho) return fail(SPH_ERR_INVALID, "rho is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    if (g->n == 0) return SPH_OK;
+    const GridDev d = make_dev(g);
+    SPH_CUDA(launch_status_reset_counters(P<DevStatus>(g->status), s));
+    SPH_CUDA(launch_density_half(d, P<int>(g->scell), rho, g->sm_count, s));
+    return SPH_OK;
+}
+
 extern "C" int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, float *rho,
                                void *stream) {
     sph_grid_s *g = grid;

@@ -51,6 +51,8 @@ cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long 
                          int *big_list, unsigned int *big_count, int sm_count, cudaStream_t s);
 
 // Appendix Eq. A5 gradient over a CSR (gradient.cu); fs: float2 scratch of n.
+// Summation density over a half stencil, rho in sorted order (density_half.cu).
+cudaError_t launch_density_half(const GridDev &g, const int *scell, float *rho, int sm_count, cudaStream_t s);
 cudaError_t launch_gradient_a5(const GridDev &g, const int *rank, const int *scell, const long long *row_ptr,
                                const int *col, int canonical, const double *f, float2 *fs, double *grad,
                                int sm_count, cudaStream_t s);

@@ -126,6 +126,7 @@ def load(build_if_missing=False):
         "sph_grid_info_get": [_vp, ctypes.POINTER(sph_grid_info)],
         "sph_grid_export": [_vp, _vp, _vp, _vp, _vp],
         "sph_grid_export_rel": [_vp, _vp, _vp, _vp],
+        "sph_density_half": [_vp, _vp, _vp],
         "sph_grid_check": [_vp, _vp],
         "sph_grid_free": [_vp],
         "sph_last_error": [],
@@ -173,7 +174,7 @@ def load(build_if_missing=False):
 def exported_symbols():
     """Names of the C-ABI entry points this binding expects."""
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
-            "sph_grid_export", "sph_grid_export_rel", "sph_grid_check", "sph_grid_free", "sph_last_error",
+            "sph_grid_export", "sph_grid_export_rel", "sph_density_half", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
@@ -250,6 +251,10 @@ def sph_grid_info_get(grid):
 
 def sph_grid_export(grid, orig_id=None, rank=None, cell_start=None, stream=None):
     _check(load().sph_grid_export(grid, _ptr(orig_id), _ptr(rank), _ptr(cell_start), _stream(stream)))
+
+
+def sph_density_half(grid, rho, stream=None):
+    _check(load().sph_density_half(grid, _ptr(rho), _stream(stream)))
 
 
 def sph_grid_export_rel(grid, rel16=None, rel32=None, stream=None):
@@ -651,6 +656,14 @@ class Grid:
         out = torch.empty(self.n, dtype=torch.int32, device=self.xyz.device)
         sph_grid_export(self.handle, out, None, None, stream)
         return out
+
+    def density_half(self, stream=None):
+        """float32[N] tensor: the summation density over a half stencil
+        (no neighbour list), in sorted order (row r is input orig_id[r])."""
+        import torch
+        rho = torch.empty(self.n, dtype=torch.float32, device=self.xyz.device)
+        sph_density_half(self.handle, rho, stream)
+        return rho
 
     def relative_coordinates(self, stream=None):
         """(rel16, rel32) in sorted order: float16[N, 4] (x, y, z, then the

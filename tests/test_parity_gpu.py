@@ -307,3 +307,18 @@ def test_large_sparse_grid(sph, dim, n, h):
     info = out["info"]
     assert info.ncell > 152 * 4 * 4096
     check_against_oracle(out, xyz, h, 2 * h, 0)
+
+
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "random3d", "faces3d", "dambreak_small"])
+def test_density_half_stencil(sph, case):
+    """The summation density over the half stencil (each pair tested once,
+    no neighbour list) against the oracle's density and the search's."""
+    xyz, h = CASES[case]()
+    out = run(sph, xyz, h, 2 * h, 0)
+    half = out["grid"].density_half().cpu().numpy().astype(np.float64)
+    rp_ref, col_ref = oracle.cll(xyz, 2 * h)
+    rho_ref = oracle.density(xyz, h, rp_ref, col_ref)
+    r = np.empty_like(rho_ref)
+    r[out["orig"]] = half
+    assert (np.abs(r - rho_ref) / rho_ref).max() <= RHO_RTOL
+    assert (np.abs(half - out["rho"]) / out["rho"]).max() <= 2e-6
