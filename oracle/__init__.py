@@ -35,6 +35,8 @@ def _load():
     lib.oracle_kernel_alpha.argtypes = [ctypes.c_int, ctypes.c_double]
     lib.oracle_kernel_w.restype = ctypes.c_double
     lib.oracle_kernel_w.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.oracle_kernel_dwdr.restype = ctypes.c_double
+    lib.oracle_kernel_dwdr.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
     lib.oracle_kernel_w_array.restype = None
     lib.oracle_kernel_w_array.argtypes = [ctypes.c_int, ctypes.c_int64, _f64p, ctypes.c_double, _f64p]
     lib.oracle_allpairs.restype = ctypes.c_int64
@@ -83,6 +85,13 @@ def kernel_w(dim, R, h):
     out = np.empty_like(R)
     _load().oracle_kernel_w_array(int(dim), R.size, _ptr(R, _f64p), float(h), _ptr(out, _f64p))
     return out
+
+
+def kernel_dwdr(dim, R, h):
+    """dW/dR of Eq. 3 (the derivative the Appendix A5 gradient uses), elementwise over R."""
+    lib = _load()
+    R = np.atleast_1d(np.asarray(R, dtype=np.float64))
+    return np.array([lib.oracle_kernel_dwdr(int(dim), float(r), float(h)) for r in R])
 
 
 def _csr(fn, xyz, kh, *extra):

@@ -11,9 +11,10 @@
  * left-to-right FP64 expression, with no fused multiply-add.
  *
  * What each function follows (section / equation of arXiv 2401.08586):
- *   oracle_kernel_alpha / oracle_kernel_w
+ *   oracle_kernel_alpha / oracle_kernel_w / oracle_kernel_dwdr
  *       cubic B-spline kernel W(R, h), Eq. 3, with alpha_d = 1/h, 15/(7 pi h^2),
- *       3/(2 pi h^3) for d = 1, 2, 3 (text under Eq. 3); R = r / h.
+ *       3/(2 pi h^3) for d = 1, 2, 3 (text under Eq. 3); R = r / h; and its
+ *       derivative dW/dR, Eq. 3 differentiated term by term.
  *   oracle_allpairs
  *       all-list search ("SPH method", all-list paragraph; Fig. 3a): every
  *       particle is compared with every other one, N(N-1) ordered comparisons,
@@ -77,8 +78,9 @@ double oracle_kernel_w(int dim, double R, double h)
     return 0.0;
 }
 
-/* dW/dR of Eq. 3 (used only by the gradient operator). */
-static double kernel_dwdr(int dim, double R, double h)
+/* dW/dR of Eq. 3 (used by the gradient operator of Appendix Eq. A5):
+ * alpha_d (-2R + 3R^2/2) on [0, 1), -alpha_d (2 - R)^2 / 2 on [1, 2), 0 beyond. */
+double oracle_kernel_dwdr(int dim, double R, double h)
 {
     double a = oracle_kernel_alpha(dim, h);
     if (R < 1.0) return a * (-2.0 * R + 1.5 * R * R);
@@ -422,7 +424,7 @@ void oracle_gradient_a5(int dim, int64_t n, const double *xyz, double h, const d
             const double *xj = xyz + j * dim;
             double r = sqrt(pair_r2(dim, xi, xj));
             if (r == 0.0) continue;
-            double dwdr = kernel_dwdr(dim, r / h, h) / h;
+            double dwdr = oracle_kernel_dwdr(dim, r / h, h) / h;
             for (int a = 0; a < dim; ++a) {
                 double dwdx = dwdr * (xi[a] - xj[a]) / r;
                 num[a] += (f[j] - f[i]) * dwdx;

@@ -272,3 +272,85 @@ def test_gradient_a5_first_order():
         inner = np.all((xyz > 0.2) & (xyz < 0.8), axis=1)
         errs.append(np.sqrt(np.mean((g[inner, 0] - 3 * xyz[inner, 0] ** 2) ** 2)))
     assert errs[1] < errs[0] * 0.75
+
+
+# ------------------------------------------- kernel derivative (Eq. 3, A5)
+
+def _golden_derivative():
+    from fractions import Fraction
+    table, a5 = [], []
+    for row in read_golden("kernel_derivative.txt"):
+        if row[0] == "A5":
+            a5.append(row[1:])
+        else:
+            table.append((Fraction(row[0]), Fraction(row[1])))
+    return table, a5
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("h", [1.0, 0.013])
+def test_kernel_derivative_hand_values(dim, h):
+    """dW/dR against Eq. 3 differentiated by hand (tests/golden/kernel_derivative.txt):
+    both branches, their junction at R = 1 and the ends of the support."""
+    a = oracle.kernel_alpha(dim, h)
+    table, _ = _golden_derivative()
+    for R, dP in table:
+        got = oracle.kernel_dwdr(dim, float(R), h)[0]
+        assert got == pytest.approx(a * float(dP), rel=1e-15, abs=1e-300), (dim, R)
+    # just below the support's end the derivative is -(2 - R)^2 / 2 -> 0
+    assert oracle.kernel_dwdr(dim, 2.0 - 1e-6, h)[0] == pytest.approx(-a * 0.5e-12, rel=1e-6)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_kernel_derivative_central_differences(dim):
+    """dW/dR against central differences of W (pinned above by closed forms and
+    its normalisation integral) at points inside both branches."""
+    h = 0.37
+    eps = 1e-6
+    for R in np.concatenate([np.linspace(0.01, 0.99, 23), np.linspace(1.01, 1.99, 23)]):
+        w_hi = oracle.kernel_w(dim, R + eps, h)[0]
+        w_lo = oracle.kernel_w(dim, R - eps, h)[0]
+        fd = (w_hi - w_lo) / (2 * eps)
+        got = oracle.kernel_dwdr(dim, R, h)[0]
+        assert got == pytest.approx(fd, rel=1e-6, abs=1e-9 * oracle.kernel_alpha(dim, h)), R
+
+
+def test_gradient_a5_hand_worked():
+    """Appendix A5 on the three-particle line of tests/golden/kernel_derivative.txt
+    (f = x^2, one neighbour in each branch of the kernel): -1/4 along x, 0 along y."""
+    from fractions import Fraction
+    _, a5 = _golden_derivative()
+    for dim, h, xi, yi, x1, y1, x2, y2, field, ex, ey in a5:
+        assert field == "x^2"
+        xyz = np.array([[float(Fraction(xi)), float(Fraction(yi))],
+                        [float(Fraction(x1)), float(Fraction(y1))],
+                        [float(Fraction(x2)), float(Fraction(y2))]])
+        f = xyz[:, 0] ** 2
+        rp, col = oracle.allpairs(xyz, 2 * float(h))
+        assert col[rp[0]:rp[1]].tolist() == [1, 2]
+        g = oracle.gradient_a5(xyz, float(h), f, rp, col)
+        assert g[0, 0] == pytest.approx(float(Fraction(ex)), rel=1e-14)
+        assert g[0, 1] == float(Fraction(ey))
+
+
+def test_gradient_a5_off_axis_against_finite_difference_weights():
+    """A5 for four particles off the axes (f = x^2 + 3 y^2), the expected value
+    built from the A5 sums with weights W' taken by central differences of the
+    pinned W (not the oracle's derivative): a wrong branch, coefficient or a
+    W in place of W' moves the ratio."""
+    h = 1.0
+    xyz = np.array([[0.0, 0.0], [0.4, 0.3], [-1.1, 0.5], [0.2, -1.3], [-0.7, -0.9]])
+    f = xyz[:, 0] ** 2 + 3 * xyz[:, 1] ** 2
+    rp, col = oracle.allpairs(xyz, 2 * h)
+    g = oracle.gradient_a5(xyz, h, f, rp, col)
+    eps = 1e-6
+    num, den = np.zeros(2), np.zeros(2)
+    for j in col[rp[0]:rp[1]]:
+        d = xyz[0] - xyz[j]
+        r = math.hypot(d[0], d[1])
+        wp = (oracle.kernel_w(2, r / h + eps, h)[0] - oracle.kernel_w(2, r / h - eps, h)[0]) / (2 * eps) / h
+        dwdx = wp * d / r
+        num += (f[j] - f[0]) * dwdx
+        den += (xyz[j] - xyz[0]) * dwdx
+    assert len(col[rp[0]:rp[1]]) == 4
+    assert np.allclose(g[0], num / den, rtol=1e-7)

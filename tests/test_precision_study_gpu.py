@@ -1,10 +1,13 @@
 """Precision study (sph_precision_study): the tiered decision is never
-wrong; FP16 absolute coordinates fail first, as Tables 1-2 report (GPU
-required)."""
+wrong; the FP16 / FP32 absolute and FP16 cell-relative wrong-decision counts
+equal, as integers, a CPU emulation of the same operation sequence with one
+IEEE rounding per step (tests/study_emulation.py); FP16 absolute coordinates
+fail first, as Tables 1-2 report (GPU required)."""
 import numpy as np
 import pytest
 
 import oracle
+import study_emulation
 from paper_2401_08586_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -20,9 +23,16 @@ def sph():
     return _sph
 
 
+EXACT = ("candidates", "neighbours", "wrong_fp16_abs", "wrong_fp32_abs", "wrong_fp16_rcll")
+
+
 def test_table1_circle(sph):
     from paper_2401_08586_gb300 import study
     rows = study.table1(sph, torch)
+    for r in rows:
+        xyz = W.circle_pairs(1.0, r["dR"], 60, dim=2, seed=0, center=(0.0, 0.0))
+        want = study_emulation.counts(xyz, 1.0, 0, 1)
+        assert {k: r[k] for k in EXACT} == want, r["dR"]
     w16 = [r["wrong_fp16_abs"] for r in rows]
     w32 = [r["wrong_fp32_abs"] for r in rows]
     for r in rows:
@@ -36,9 +46,13 @@ def test_table1_circle(sph):
 
 def test_table2_random(sph):
     from paper_2401_08586_gb300 import study
-    rows = study.table2(sph, torch, ds_list=[0.01, 0.004, 0.002])
+    rows = study.table2(sph, torch, ds_list=[0.01, 0.005, 0.002])
     for r in rows:
         assert r["wrong_tiered"] == 0
+    for r in rows[:2]:
+        xyz = W.random_uniform(r["n"], 2, 1)
+        want = study_emulation.counts(xyz, 2 * 1.2 * r["ds"])
+        assert {k: r[k] for k in EXACT} == want, r["ds"]
     p16 = [r["pct"]["wrong_fp16_abs"] for r in rows]
     prc = [r["pct"]["wrong_fp16_rcll"] for r in rows]
     assert p16[0] < p16[-1] and p16[-1] > 0.05

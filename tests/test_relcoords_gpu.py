@@ -8,13 +8,11 @@ The fused multiply-add is evaluated exactly with rationals and rounded once
 (Python's float(Fraction) rounds to nearest).  Covers the particle at the
 lower bound (s = 0), the half cell next to it (s < 1), the upper clamp, and a
 grid far from the origin (the subtraction route).  GPU required."""
-from fractions import Fraction
-import math
-
 import numpy as np
 import pytest
 
 from paper_2401_08586_gb300 import workloads as W
+from relref import reference
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,34 +25,6 @@ def sph():
     from paper_2401_08586_gb300 import sph as _sph
     _sph.load()
     return _sph
-
-
-def reference(xyz, kh):
-    """FP32 and FP16 relative coordinates of every input particle."""
-    n, dim = xyz.shape
-    hc = kh * (1.0 + 2.0 ** -30)
-    t = 2.0 / hc
-    lo, hi = xyz.min(axis=0), xyz.max(axis=0)
-    nk = [max(1, int(math.ceil((hi[k] - lo[k]) / hc))) for k in range(dim)]
-    fma = all(max(abs(lo[k]), abs(lo[k] + nk[k] * hc)) * t <= 131072.0 for k in range(dim))
-    f32 = np.zeros((n, 4), dtype=np.float32)
-    cx = None
-    for k in range(dim):
-        b = -lo[k] * t
-        if fma:
-            ft, fb = Fraction(t), Fraction(b)
-            s = np.array([float(Fraction(float(x)) * ft + fb) for x in xyz[:, k]])
-        else:
-            s = (xyz[:, k] - lo[k]) * t
-        c = np.minimum(np.floor(s).astype(np.int64) >> 1, nk[k] - 1)
-        c = np.maximum(c, 0)
-        if k == 0:
-            cx = c
-        a = s - (2 * c + 1).astype(np.float64)
-        f32[:, k] = a.astype(np.float32)
-    f16 = f32.astype(np.float16).view(np.uint16).copy()
-    f16[:, 3] = (cx & 0xFFFF).astype(np.uint16)
-    return f32, f16, fma
 
 
 def check(sph, xyz, h, expect_fma):
