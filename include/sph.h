@@ -267,7 +267,10 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *     chosen from the neighbours per particle, 0 sparse (up to 672 kept
  *     candidates per pass of a tile, 20 resident warps per SM, output staged
  *     for tiles of up to ~80 neighbours per row), 1 dense (832 kept
- *     candidates, 16 warps).  Same results either way. */
+ *     candidates, 16 warps), 2 whole-pass (512 kept candidates, FP32
+ *     coordinates of all of them staged so each lane walks its bits once per
+ *     tile, 18 warps).  Same CSR either way; the density's last bits follow
+ *     the summation order of the shape. */
 #define SPH_OPT_TILE_SHAPE 3
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 

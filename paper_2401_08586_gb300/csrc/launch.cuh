@@ -79,7 +79,7 @@ cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool 
 // Shared-memory shape of a tile-search launch: TILE_SPARSE (672 kept
 // candidates per pass, 20 warps per SM) or TILE_DENSE (832, 16 per SM), and
 // extra dynamic shared memory for output staging.
-enum { TILE_SPARSE = 0, TILE_DENSE = 1 };
+enum { TILE_SPARSE = 0, TILE_DENSE = 1, TILE_WHOLE = 2 };
 struct TileLaunch {
     int shape;
     int extra;

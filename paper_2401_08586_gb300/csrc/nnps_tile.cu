@@ -69,6 +69,11 @@ struct TileCfg {
     static constexpr int WSM = WSM_;
     static constexpr int WB = WB_;  // bits in flight per lane in the walk (independent loads and arithmetic)
     static constexpr int NWORD = CMAX_ / 32;
+    // Bitmask matrix: NWORD + 1 words per lane.  With an even row stride the
+    // words of lanes l and l + 16 in one column share a bank; lanes 16..31
+    // then start one word later (in the padding word), which puts the 32
+    // lanes' words of a column in 32 different banks.
+    static constexpr int SSHIFT = (NWORD + 1) % 2 == 0 ? 1 : 0;
     static_assert(CMAX_ % 32 == 0 && WIN_ % 32 == 0 && WIN_ <= CMAX_, "tile shape");
     static_assert(WSM_ % WPB_ == 0, "warps per CTA");
 };
@@ -79,6 +84,8 @@ using TileDense = TileCfg<832, 256, 2, 16, 4>;
 template <class C>
 struct TileSmem {
     unsigned int S[TW][C::NWORD + 1];
+    __device__ __forceinline__ unsigned int &bits(int lane, int word) { return S[lane][word + C::SSHIFT * (lane >> 4)]; }
+    __device__ __forceinline__ unsigned int bits(int lane, int word) const { return S[lane][word + C::SSHIFT * (lane >> 4)]; }
     int jall[C::CMAX];  // kept candidates: sorted index
     short selfpos[TW];  // kept slot of each lane's own particle (-1: not in this fill)
     // candidate rows r: sorted index minus flat index of the row's candidates,
@@ -282,7 +289,7 @@ __device__ __forceinline__ void stage_window(TileSmem<C> &S, const GridDev &g, i
 }
 
 // FP16 tests of the window (nwin words of 32) against the lane's home
-// particle; bit per kept candidate into S.S[lane][wbase + gi].  The lane's
+// particle; bit per kept candidate into S.bits(lane, wbase + gi).  The lane's
 // own particle (window slot self_slot, or -1) is left out.
 template <int DIM, class C>
 __device__ __forceinline__ unsigned int test_window(TileSmem<C> &S, const Home &h, bool active, unsigned int negT,
@@ -309,7 +316,7 @@ __device__ __forceinline__ unsigned int test_window(TileSmem<C> &S, const Home &
         }
         if ((self_slot >> 5) == gi) word &= ~(1u << (self_slot & 31));
         word = active ? word : 0u;
-        S.S[lane][wbase + gi] = word;
+        S.bits(lane, wbase + gi) = word;
         nem |= (word != 0u ? 1u : 0u) << gi;
     }
     __syncwarp();
@@ -321,23 +328,36 @@ enum { PASS_COUNT = 0, PASS_EMIT = 1 };
 // Walk the lane's bits in words [wbase, wbase + nw) of the window: FP32
 // re-decision (FP64 inside the band) and density; rejected bits cleared.
 // PASS_EMIT writes the neighbours to col[rp + cnt] instead of summing.
-// Up to WB set bits of the lane's words [wbase + gi, wbase + nw), in order:
-// positions p[k] (window-local candidate slots) with v[k] marking valid ones.
-// nem: the lane's words still to visit that hold at least one bit (bit gi for
-// word wbase + gi), so advancing to the next word needs no loop.
-template <int WB, class C>
-__device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, int wbase, unsigned int &nem, int &gi,
-                                          unsigned int &w, int (&p)[WB], bool (&v)[WB]) {
+// The lane's set bits of words [wbase, wbase + nw) in ascending order, up to
+// WB per call: positions p[k] (window-local candidate slots) with v[k]
+// marking valid ones (v[0] false: no bits left).  State: the current word w
+// (its index gi), the next non-empty word wn (index gn), prefetched once per
+// call, and nem, the lane's non-empty words not yet fetched (bit q for word
+// wbase + q).  A word that runs out mid-call is replaced by a register move;
+// a call may return fewer than WB bits when two words run out in it, unless
+// EACH (refill before every bit: for long calls).
+struct BitCursor {
+    unsigned int w = 0u, wn = 0u, nem = 0u;
+    int gi = 0, gn = 0;
+};
+template <int WB, class C, bool EACH = false>
+__device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, int wbase, BitCursor &b, int (&p)[WB],
+                                          bool (&v)[WB]) {
 #pragma unroll
     for (int k = 0; k < WB; ++k) {
-        if (w == 0u && nem != 0u) {
-            gi = __ffs(nem) - 1;
-            nem &= nem - 1u;
-            w = S.S[lane][wbase + gi];
+        if ((k == 0 || EACH) && b.wn == 0u && b.nem != 0u) {
+            b.gn = __ffs(b.nem) - 1;
+            b.nem &= b.nem - 1u;
+            b.wn = S.bits(lane, wbase + b.gn);
         }
-        v[k] = w != 0u;
-        p[k] = gi * 32 + (__ffs(w) - 1);
-        w &= w - 1u;
+        if (b.w == 0u) {
+            b.w = b.wn;
+            b.gi = b.gn;
+            b.wn = 0u;
+        }
+        v[k] = b.w != 0u;
+        p[k] = b.gi * 32 + (__ffs(b.w) - 1);
+        b.w &= b.w - 1u;
     }
 }
 
@@ -354,63 +374,74 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 // The lane's own particle has been removed from its bits by test_window, so
 // every remaining bit is a pair j != i.  The common case (FP32 says
 // "neighbour") runs without branches; pairs the FP32 tier rejects or leaves
-// in its band go through a warp-uniform slow path.
+// in its band go through a warp-uniform slow path.  K bits (window-local
+// slots p[k], valid v[k]) of the lane's row.
+template <int DIM, int PASS, class C, int K>
+__device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase,
+                                          const int (&p)[K], const bool (&v)[K], int &cnt, float &acc, int *col,
+                                          long long rp, unsigned int &n32, unsigned int &n64) {
+    const int lane = threadIdx.x & 31;
+    float r2[K];
+    int jj[K];
+    bool in[K];
+    bool odd = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 c = S.f32[v[k] ? p[k] : 0];
+        jj[k] = __float_as_int(c.w);
+        const float d0 = __fsub_rn(c.x, h.x32);
+        const float d1 = __fsub_rn(c.y, h.y32);
+        const float d2 = __fsub_rn(c.z, h.z32);
+        r2[k] = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
+        in[k] = v[k] && r2[k] < g.t32_in;
+        odd |= v[k] && !in[k];
+    }
+    if (__any_sync(0xffffffffu, odd)) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (v[k] && !in[k]) {
+                if (r2[k] <= g.t32_out) {
+                    ++n64;
+                    in[k] = fp64_tier<DIM>(g, h.i, jj[k]);
+                } else {
+                    ++n32;
+                }
+                if (!in[k]) S.bits(lane, wbase + (p[k] >> 5)) &= ~(1u << (p[k] & 31));
+            }
+        }
+    }
+    if (PASS == PASS_EMIT) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (in[k]) col[rp + cnt++] = jj[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
+            acc += in[k] ? wk : 0.f;
+        }
+    }
+}
+
+// Walk the lane's bits of one window in candidate order (the emit pass
+// needs it: columns ascending).
 template <int DIM, int PASS, class C>
 __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase, int nwin,
                                             unsigned int nem, int &cnt, float &acc, int *col, long long rp,
                                             unsigned int &n32, unsigned int &n64) {
     const int lane = threadIdx.x & 31;
-    int gi = 0;
-    unsigned int w = 0u;
+    BitCursor cur;
+    cur.nem = nem;
     while (true) {
         int p[C::WB];
         bool v[C::WB];
-        next_bits<C::WB, C>(S, lane, wbase, nem, gi, w, p, v);
+        next_bits<C::WB, C>(S, lane, wbase, cur, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
-        float r2[C::WB];
-        int jj[C::WB];
-        bool in[C::WB];
-        bool odd = false;
-#pragma unroll
-        for (int k = 0; k < C::WB; ++k) {
-            const float4 c = S.f32[v[k] ? p[k] : 0];
-            jj[k] = __float_as_int(c.w);
-            const float d0 = __fsub_rn(c.x, h.x32);
-            const float d1 = __fsub_rn(c.y, h.y32);
-            const float d2 = __fsub_rn(c.z, h.z32);
-            r2[k] = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
-            in[k] = v[k] && r2[k] < g.t32_in;
-            odd |= v[k] && !in[k];
-        }
-        if (__any_sync(0xffffffffu, odd)) {
-#pragma unroll
-            for (int k = 0; k < C::WB; ++k) {
-                if (v[k] && !in[k]) {
-                    if (r2[k] <= g.t32_out) {
-                        ++n64;
-                        in[k] = fp64_tier<DIM>(g, h.i, jj[k]);
-                    } else {
-                        ++n32;
-                    }
-                    if (!in[k]) S.S[lane][wbase + (p[k] >> 5)] &= ~(1u << (p[k] & 31));
-                }
-            }
-        }
-        if (PASS == PASS_EMIT) {
-#pragma unroll
-            for (int k = 0; k < C::WB; ++k)
-                if (in[k]) col[rp + cnt++] = jj[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < C::WB; ++k) {
-                const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
-                acc += in[k] ? wk : 0.f;
-            }
-        }
+        walk_bits<DIM, PASS, C, C::WB>(S, g, h, wbase, p, v, cnt, acc, col, rp, n32, n64);
     }
     if (PASS == PASS_COUNT) {
         // the neighbours of this window: its bits that survived the re-decision
-        for (int q = 0; q < nwin; ++q) cnt += __popc(S.S[lane][wbase + q]);
+        for (int q = 0; q < nwin; ++q) cnt += __popc(S.bits(lane, wbase + q));
     }
     __syncwarp();
 }
@@ -480,15 +511,13 @@ __device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home
 template <class C>
 __device__ __forceinline__ void emit_bits(const TileSmem<C> &S, int lane, int nw, long long pos, unsigned short *stg,
                                           int *col, const int *jall) {
-    unsigned int nem = 0;
-    for (int q = 0; q < nw; ++q) nem |= (S.S[lane][q] != 0u ? 1u : 0u) << q;
-    int gi = 0;
-    unsigned int w = 0u;
+    BitCursor cur;
+    for (int q = 0; q < nw; ++q) cur.nem |= (S.bits(lane, q) != 0u ? 1u : 0u) << q;
     constexpr int EB = 8;
     while (true) {
         int p[EB];
         bool v[EB];
-        next_bits<EB, C>(S, lane, 0, nem, gi, w, p, v);
+        next_bits<EB, C, true>(S, lane, 0, cur, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
         if (stg != nullptr) {
 #pragma unroll
@@ -573,8 +602,9 @@ __global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
         // A simple tile whose row segment fits the staging area lays its
         // output out in shared memory before it needs its CSR offset, so the
         // wait on earlier tiles overlaps that work.
-        const bool staged = simple && col != nullptr && agg <= stg_slots;
+        const int *jl = S.jall;
         unsigned short *stg = reinterpret_cast<unsigned short *>(&S.code[0]);
+        const bool staged = simple && col != nullptr && agg <= stg_slots;
         if (staged) emit_bits<C>(S, lane, mine ? (kept + 31) >> 5 : 0, rstart, stg, nullptr, nullptr);
         const long long pre = look_back_resolve(tstate, t, agg, &g0.status->flags);
         const bool wc = col != nullptr && pre + agg <= cap;
@@ -588,11 +618,11 @@ __global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
         if (staged) {
             // consecutive lanes on consecutive entries of the tile's segment
 #pragma unroll 4
-            for (int e = lane; e < agg; e += 32) col[pre + e] = S.jall[stg[e]];
+            for (int e = lane; e < agg; e += 32) col[pre + e] = jl[stg[e]];
             __syncwarp();
         } else if (simple) {
             // segment larger than the staging area: rows straight to col
-            emit_bits<C>(S, lane, mine ? (kept + 31) >> 5 : 0, pre + rstart, nullptr, col, S.jall);
+            emit_bits<C>(S, lane, mine ? (kept + 31) >> 5 : 0, pre + rstart, nullptr, col, jl);
         } else {
             // emit pass: same decisions again, written straight to the rows
             int ecnt = 0;
