@@ -222,12 +222,12 @@ int sph_precision_study(sph_grid_t grid, int64_t row_begin, int64_t row_end, sph
  * and calls no allocating routine.  (The paper has no counterpart; this is an
  * interface addition.)
  *
- * Its working memory (cell index per particle, tile list, look-back state:
- * about 7.1 MiB) is one fixed array inside the library.  Every GPU that loads
- * the library holds that array until the process exits.  The first call on
- * each device looks up the array's device address with
- * cudaGetSymbolAddress (no allocation) and caches it; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * Its working memory (tile list, its row offsets, look-back state: about 3.1
+ * MiB) is one fixed array inside the library.  Every GPU that loads the
+ * library holds that array until the process exits.  The first call in each
+ * CUDA context (per device; again after a device reset) looks up the array's
+ * device address with cudaGetSymbolAddress (no allocation) and caches it;
+ * make that first call before any stream capture.  All calls share the one array and it keeps the
  * last call's contents (the call clears what must start at zero), so calls
  * whose GPU work overlaps -- different streams, or concurrent host threads on
  * one device -- race and give wrong results: serialise them.
@@ -272,6 +272,15 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *     tile, 18 warps).  Same CSR either way; the density's last bits follow
  *     the summation order of the shape. */
 #define SPH_OPT_TILE_SHAPE 3
+/*   SPH_OPT_TEST_LOOKBACK: for tests of the bounded device waits only.  0
+ *     (default): normal queries.  k in 1 .. 2^20: the next queries run the
+ *     single-pass tile search with its first tile left out, so every later
+ *     tile's look-back wait on it runs out after k polls (each at most ~1 us
+ *     apart); the query's results are then wrong by design, nothing is
+ *     written at or past col_capacity, the query reports SPH_ERR_TIMEOUT (or
+ *     sph_grid_check does) and the GPU context stays usable.  Set 0 to go
+ *     back to normal queries. */
+#define SPH_OPT_TEST_LOOKBACK 4
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 
 /* Fill *info (host) with the grid's sizes and device pointers.  The pointers

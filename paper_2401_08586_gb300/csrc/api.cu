@@ -35,6 +35,7 @@ struct sph_grid_s {
     int staging = -1;       // extra staging bytes of the tile search (SPH_OPT_STAGING; -1: automatic)
     int tile_shape = -1;    // shared-memory shape of the tile search (SPH_OPT_TILE_SHAPE; -1: automatic)
     double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
+    int test_lookback = 0;  // SPH_OPT_TEST_LOOKBACK: > 0 skips the first tile, waits give up after that many polls
     DevBuf rel64, rel64u;   // FP64 relative coordinates kept across time steps (cell / input order)
     DevBuf fsplit;          // gradient: the field as float hi + lo in cell order
     DevBuf study;           // precision study counters
@@ -278,6 +279,43 @@ extern "C" int sph_advance(sph_grid_t grid, const double *xyz_new, const double 
     return SPH_OK;
 }
 
+// Single pass, one warp per 32-particle row tile, look-back across tiles
+// (nnps_tile.cu), in cell order: row pointers always; columns and the fused
+// density when col / rho are given (col == NULL: the count only).
+static int run_tile_search(sph_grid_s *g, long long *rp_cell, int *col, long long cap, float *rho, bool test_lb,
+                           cudaStream_t s) {
+    const long long n = g->n;
+    const long long nrow = (long long)g->nk[1] * g->nk[2];
+    const long long ntiles_max = tiles_max(n, g->ncell, nrow);
+    SPH_TRY(ensure(g->tcount, nrow * sizeof(int), s));
+    SPH_TRY(ensure(g->toff, (nrow + 1) * sizeof(long long), s));
+    SPH_TRY(ensure(g->tiles, ntiles_max * sizeof(int4), s));
+    // look-back state of the search (ntiles_max entries), then of the
+    // tile-list builder's chunks of rows (at most nrow + 1), cleared at once
+    const long long nstate = ntiles_max + nrow + 1;
+    SPH_TRY(ensure(g->tstate, nstate * sizeof(unsigned long long), s));
+    SPH_CUDA(cudaMemsetAsync(g->tstate.p, 0, nstate * sizeof(unsigned long long), s));
+    unsigned long long *tstate = P<unsigned long long>(g->tstate);
+    GridDev d = make_dev(g);
+    if (test_lb) d.spin_limit = g->test_lookback;
+    SPH_CUDA(launch_tiles(d, true, P<int>(g->tcount), P<long long>(g->toff), g->scan_tmp.p, P<int4>(g->tiles),
+                          tstate + ntiles_max, g->sm_count, s));
+    const TileLaunch tv =
+        tile_choose_grid(g->last_nbr, n, g->ncell, g->p.dim, g->p.kh, g->hc, g->tile_shape, g->staging);
+    SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell, col,
+                              cap, rho, tstate, tv, true, g->sm_count, s));
+    return SPH_OK;
+}
+
+// nnz of a finished cell-order search (rp_cell[n]); synchronises the stream.
+static int read_nnz(sph_grid_s *g, const long long *rp_cell, long long *nnz) {
+    SPH_CUDA(cudaMemcpyAsync(&g->h_status->nnz, rp_cell + g->n, sizeof(long long), cudaMemcpyDeviceToHost, g->stream));
+    SPH_CUDA(cudaStreamSynchronize(g->stream));
+    *nnz = g->h_status->nnz;
+    if (g->n > 0) g->last_nbr = (double)*nnz / (double)g->n;
+    return SPH_OK;
+}
+
 extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity,
                               int64_t *nnz_out, float *rho, void *stream) {
     sph_grid_s *g = grid;
@@ -297,63 +335,37 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         return SPH_OK;
     }
     GridDev d = make_dev(g);
-    SPH_CUDA(launch_status_reset_counters(P<DevStatus>(g->status), s));
+    const bool test_lb = g->test_lookback > 0;
+    SPH_CUDA(launch_status_reset_counters(P<DevStatus>(g->status), s, test_lb ? 1ull : 0ull));
     SPH_TRY(ensure(g->rowcnt, n * sizeof(int), s));
     const bool canonical = g->p.order == SPH_ORDER_CANONICAL;
     const int prec = g->p.precision;
+    // the single-pass tile search serves every FP16-RCLL query unless another
+    // search variant is asked for (SPH_OPT_FUSED 0: two passes; 2: one CTA per
+    // cell, cell-order queries with columns only)
+    const bool tile = prec == SPH_PREC_FP16_RCLL && (g->fused_enabled == 1 || test_lb);
     long long *rp_cell = reinterpret_cast<long long *>(row_ptr);
     if (canonical) {
         SPH_TRY(ensure(g->tmp_rp, (n + 1) * sizeof(long long), s));
         rp_cell = P<long long>(g->tmp_rp);
     }
-    const bool fused = !canonical && col != nullptr && prec == SPH_PREC_FP16_RCLL && g->fused_enabled;
-    if (fused && g->fused_enabled == 2) {
-        // single pass, one CTA per cell, row offsets by look-back across cells
-        SPH_TRY(ensure(g->tstate, (size_t)g->ncell * sizeof(unsigned long long), s));
-        SPH_CUDA(launch_nnps_fused(d, rp_cell, col, col_capacity, rho, P<unsigned long long>(g->tstate),
-                                   P<int>(g->rowcnt), g->sm_count, s));
-    } else if (fused) {
-        // single pass, one warp per 32-particle row tile, look-back across tiles
-        const long long nrow = (long long)g->nk[1] * g->nk[2];
-        const long long ntiles_max = tiles_max(n, g->ncell, nrow);
-        SPH_TRY(ensure(g->tcount, nrow * sizeof(int), s));
-        SPH_TRY(ensure(g->toff, (nrow + 1) * sizeof(long long), s));
-        SPH_TRY(ensure(g->tiles, ntiles_max * sizeof(int4), s));
-        // look-back state of the search (ntiles_max entries), then of the
-        // tile-list builder's chunks of rows (at most nrow + 1), cleared at once
-        const long long nstate = ntiles_max + nrow + 1;
-        SPH_TRY(ensure(g->tstate, nstate * sizeof(unsigned long long), s));
-        SPH_CUDA(cudaMemsetAsync(g->tstate.p, 0, nstate * sizeof(unsigned long long), s));
-        unsigned long long *tstate = P<unsigned long long>(g->tstate);
-        d = make_dev(g);
-        SPH_CUDA(launch_tiles(d, P<int>(g->scell), P<int>(g->scell_x), false, P<int>(g->tcount),
-                              P<long long>(g->toff), g->scan_tmp.p, P<int4>(g->tiles), tstate + ntiles_max,
-                              g->sm_count, s));
-        // neighbours per particle: the last measured value, else the
-        // uniform-density estimate (particles per cell x the search sphere's
-        // volume in cells)
-        double nbr = g->last_nbr;
-        if (nbr <= 0) {
-            const double ppc = (double)n / (double)g->ncell, r = g->p.kh / g->hc;
-            nbr = g->p.dim == 3 ? ppc * 4.18879 * r * r * r : ppc * 3.14159 * r * r;
-        }
-        TileLaunch tv = tile_choose(nbr, g->tile_shape);
-        if (g->staging >= 0) tv.extra = g->staging;
-        SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell,
-                                  col, col_capacity, rho, tstate, tv, true, g->sm_count, s));
-    } else {
-        SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
-        SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
-    }
     if (!canonical) {
-        if (col && !fused)
-            SPH_CUDA(launch_nnps(d, prec, 1, nullptr, rp_cell, col, col_capacity, rho, g->sm_count, s));
+        const bool cell_cta = col != nullptr && prec == SPH_PREC_FP16_RCLL && g->fused_enabled == 2 && !test_lb;
+        if (cell_cta) {
+            // single pass, one CTA per cell, row offsets by look-back across cells
+            SPH_TRY(ensure(g->tstate, (size_t)g->ncell * sizeof(unsigned long long), s));
+            SPH_CUDA(launch_nnps_fused(d, rp_cell, col, col_capacity, rho, P<unsigned long long>(g->tstate),
+                                       P<int>(g->rowcnt), g->sm_count, s));
+        } else if (tile) {
+            SPH_TRY(run_tile_search(g, rp_cell, col, col ? col_capacity : 0, rho, test_lb, s));
+        } else {
+            SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
+            SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
+            if (col) SPH_CUDA(launch_nnps(d, prec, 1, nullptr, rp_cell, col, col_capacity, rho, g->sm_count, s));
+        }
         if (nnz_out) {
-            SPH_CUDA(cudaMemcpyAsync(&g->h_status->nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             long long nnz_host = 0;
-            SPH_CUDA(cudaStreamSynchronize(s));
-            nnz_host = g->h_status->nnz;
-            if (n > 0) g->last_nbr = (double)nnz_host / (double)n;
+            SPH_TRY(read_nnz(g, rp_cell, &nnz_host));
             SPH_TRY(read_status(g));
             *nnz_out = nnz_host;
             int rc = status_to_code(g->h_status->flags);
@@ -364,12 +376,42 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         }
         return SPH_OK;
     }
-    // Canonical order: learn nnz first (this path always synchronises).
+    // Canonical order: search in cell order into the grid's own buffers, then
+    // permute the rows, map the columns to input indices and sort each row
+    // (this path always synchronises: it needs nnz on the host).
     long long nnz = 0;
-    SPH_CUDA(cudaMemcpyAsync(&g->h_status->nnz, rp_cell + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaStreamSynchronize(s));
-    nnz = g->h_status->nnz;
-    g->last_nbr = (double)nnz / (double)n;
+    bool have_cols = false;  // tmp_col / tmp_rho already hold the cell-order result
+    if (tile && col) {
+        // capacity guess from the last query (else the uniform-density
+        // estimate), one more search if the guess was short
+        double nbr = g->last_nbr;
+        if (nbr <= 0) {
+            const double ppc = (double)n / (double)g->ncell, r = g->p.kh / g->hc;
+            nbr = g->p.dim == 3 ? ppc * 4.18879 * r * r * r : ppc * 3.14159 * r * r;
+        }
+        long long cap_t = (long long)(nbr * (double)n * 1.1) + 4096;
+        SPH_TRY(ensure(g->tmp_col, (size_t)cap_t * sizeof(int), s));
+        cap_t = (long long)(g->tmp_col.cap / sizeof(int));
+        if (rho) SPH_TRY(ensure(g->tmp_rho, n * sizeof(float), s));
+        SPH_TRY(run_tile_search(g, rp_cell, P<int>(g->tmp_col), cap_t, rho ? P<float>(g->tmp_rho) : nullptr, test_lb,
+                                s));
+        SPH_TRY(read_nnz(g, rp_cell, &nnz));
+        have_cols = nnz <= cap_t;
+        if (!have_cols && nnz <= col_capacity) {
+            SPH_TRY(ensure(g->tmp_col, (size_t)nnz * sizeof(int), s));
+            SPH_CUDA(launch_status_reset_counters(P<DevStatus>(g->status), s, test_lb ? 1ull : 0ull));
+            SPH_TRY(run_tile_search(g, rp_cell, P<int>(g->tmp_col), nnz, rho ? P<float>(g->tmp_rho) : nullptr,
+                                    test_lb, s));
+            have_cols = true;
+        }
+    } else if (tile) {
+        SPH_TRY(run_tile_search(g, rp_cell, nullptr, 0, nullptr, test_lb, s));
+        SPH_TRY(read_nnz(g, rp_cell, &nnz));
+    } else {
+        SPH_CUDA(launch_nnps(d, prec, 0, P<int>(g->rowcnt), nullptr, nullptr, 0, nullptr, g->sm_count, s));
+        SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp_cell, n, g->scan_tmp.p, s));
+        SPH_TRY(read_nnz(g, rp_cell, &nnz));
+    }
     if (nnz_out) *nnz_out = nnz;
     if (col && nnz > col_capacity) {
         SPH_TRY(launch_canon((int)n, P<int>(g->rank), P<int>(g->orig_id), rp_cell, nullptr, nullptr,
@@ -381,14 +423,14 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         SPH_CUDA(cudaStreamSynchronize(s));
         return fail(SPH_ERR_CAPACITY, "nnz %lld exceeds col_capacity %lld", nnz, (long long)col_capacity);
     }
-    if (col) {
+    if (col && !have_cols) {
         SPH_TRY(ensure(g->tmp_col, (nnz > 0 ? nnz : 1) * sizeof(int), s));
         if (rho) SPH_TRY(ensure(g->tmp_rho, n * sizeof(float), s));
         SPH_CUDA(launch_nnps(d, prec, 1, nullptr, rp_cell, P<int>(g->tmp_col), nnz, rho ? P<float>(g->tmp_rho) : nullptr,
                              g->sm_count, s));
     }
     // row lengths are needed again: rowcnt is reused as scratch by launch_canon
-    SPH_CUDA(launch_canon((int)n, P<int>(g->rank), P<int>(g->orig_id), rp_cell, P<int>(g->tmp_col),
+    SPH_CUDA(launch_canon((int)n, P<int>(g->rank), P<int>(g->orig_id), rp_cell, col ? P<int>(g->tmp_col) : nullptr,
                           rho ? P<float>(g->tmp_rho) : nullptr, P<int>(g->rowcnt), g->scan_tmp.p,
                           reinterpret_cast<long long *>(row_ptr), col, rho, P<int>(g->big_list),
                           &P<DevStatus>(g->status)->big_cells, g->sm_count, s));
@@ -530,6 +572,11 @@ extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
         g->tile_shape = (int)value;
         return SPH_OK;
     }
+    if (option == SPH_OPT_TEST_LOOKBACK) {
+        if (value < 0 || value > (1 << 20)) return fail(SPH_ERR_INVALID, "SPH_OPT_TEST_LOOKBACK takes 0 .. 2^20");
+        g->test_lookback = (int)value;
+        return SPH_OK;
+    }
     if (option == SPH_OPT_STAGING) {
         if (value < -1 || value > 65536 || (value > 0 && value % 16 != 0))
             return fail(SPH_ERR_INVALID, "SPH_OPT_STAGING takes -1 or a multiple of 16 in [0, 65536]");
@@ -638,12 +685,16 @@ int grid_view(sph_grid_t grid, GridView *v) {
     v->order = g->p.order;
     v->n = g->n;
     v->nrow = (long long)g->nk[1] * g->nk[2];
+    const TileLaunch tv =
+        tile_choose_grid(g->last_nbr, g->n, g->ncell, g->p.dim, g->p.kh, g->hc, g->tile_shape, g->staging);
+    v->tile_shape = tv.shape;
+    v->tile_extra = tv.extra;
     return SPH_OK;
 }
 
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
-void reset_counters_async(DevStatus *st, cudaStream_t s) { launch_status_reset_counters(st, s); }
+cudaError_t reset_counters_async(DevStatus *st, cudaStream_t s) { return launch_status_reset_counters(st, s); }
 
 }  // namespace sph
 

@@ -148,11 +148,12 @@ __global__ void k_status_init(DevStatus *st) {
 }
 
 // Per-query state: the tier counters, the tile ticket and the flags a query
-// raises (capacity, timeout); the binning flags stay.
-__global__ void k_status_reset_counters(DevStatus *st) {
+// raises (capacity, timeout); the binning flags stay.  first_ticket is 0
+// except in the bounded-wait test (SPH_OPT_TEST_LOOKBACK), which starts at 1.
+__global__ void k_status_reset_counters(DevStatus *st, unsigned long long first_ticket) {
     st->fp32_pairs = 0;
     st->fp64_pairs = 0;
-    st->ticket = 0;
+    st->ticket = first_ticket;
     st->flags &= ~(ST_CAPACITY | ST_TIMEOUT);
 }
 
@@ -162,9 +163,9 @@ cudaError_t launch_status_init(DevStatus *st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_status_reset_counters(DevStatus *st, cudaStream_t s) {
+cudaError_t launch_status_reset_counters(DevStatus *st, cudaStream_t s, unsigned long long first_ticket) {
     note_launch(1);
-    k_status_reset_counters<<<1, 1, 0, s>>>(st);
+    k_status_reset_counters<<<1, 1, 0, s>>>(st, first_ticket);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ void set_divisors(GridDev &d);
 
 // Host launchers of the status-record kernels.
 cudaError_t launch_status_init(DevStatus *st, cudaStream_t s);
-cudaError_t launch_status_reset_counters(DevStatus *st, cudaStream_t s);
+cudaError_t launch_status_reset_counters(DevStatus *st, cudaStream_t s, unsigned long long first_ticket = 0);
 
 }  // namespace sph
 

@@ -69,17 +69,17 @@ cudaError_t launch_nnps_fused(const GridDev &g, long long *row_ptr, int *col, lo
                               unsigned long long *tstate, int *rowcnt, int sm_count, cudaStream_t s);
 
 // Single-pass search, one warp per row tile (nnps_tile.cu).
-// need_cell_x: compute scell_x from scell first (binning already wrote it
-// for grids; the no-allocation path keeps its own copy).  cstate (nrow + 1
-// zeroed entries, or nullptr): build the list in one launch with a
+// Tile list: span_limited tiles (at most TILE_SPAN cells each; the search's
+// own list) or plain runs of 32 particles per row (the no-allocation path,
+// whose fixed scratch bounds the tile count by n / 32 + nrow + 1).  cstate
+// (nrow + 1 zeroed entries, or nullptr): build the list in one launch with a
 // look-back over chunks of rows instead of count, scan and write.
-cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
-                         long long *toff, void *scan_tmp, int4 *tiles, unsigned long long *cstate, int sm_count,
-                         cudaStream_t s);
+cudaError_t launch_tiles(const GridDev &g, bool span_limited, int *tcount, long long *toff, void *scan_tmp,
+                         int4 *tiles, unsigned long long *cstate, int sm_count, cudaStream_t s);
 // Shared-memory shape of a tile-search launch: TILE_SPARSE (672 kept
 // candidates per pass, 20 warps per SM) or TILE_DENSE (832, 16 per SM), and
 // extra dynamic shared memory for output staging.
-enum { TILE_SPARSE = 0, TILE_DENSE = 1, TILE_WHOLE = 2 };
+enum { TILE_SPARSE = 0, TILE_DENSE = 1 };
 struct TileLaunch {
     int shape;
     int extra;
@@ -89,5 +89,9 @@ cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *
                              unsigned long long *tstate, TileLaunch v, bool zeroed, int sm_count, cudaStream_t s);
 // Shape (shape < 0: chosen from nbr) and staging for about nbr neighbours per particle.
 TileLaunch tile_choose(double neighbours_per_particle, int shape);
+// The same for a grid: its last measured neighbours per particle (else the
+// uniform-density estimate) and its SPH_OPT_TILE_SHAPE / SPH_OPT_STAGING settings.
+TileLaunch tile_choose_grid(double last_nbr, long long n, long long ncell, int dim, double kh, double hc,
+                            int tile_shape, int staging);
 
 }  // namespace sph

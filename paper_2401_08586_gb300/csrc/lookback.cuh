@@ -33,10 +33,11 @@ __device__ __forceinline__ void look_back_publish(unsigned long long *tstate, lo
 // Sum of all earlier units' totals, by looking back over their published
 // states 32 at a time (stopping at the first inclusive prefix); then publish
 // unit t's inclusive prefix.  Called by a whole warp.  Every wait is bounded:
-// after LOOKBACK_SPIN_LIMIT polls the unit records ST_TIMEOUT in *flags and
-// continues.
+// after spin_limit polls (each at most ~1 us apart) the unit records
+// ST_TIMEOUT in *flags, publishes the prefix it has (so later units do not
+// wait on the missing one) and continues.
 __device__ __forceinline__ long long look_back_resolve(unsigned long long *tstate, long long t, long long agg,
-                                                       unsigned int *flags) {
+                                                       unsigned int *flags, int spin_limit = LOOKBACK_SPIN_LIMIT) {
     const int lane = threadIdx.x & 31;
     if (t == 0) return 0;
     long long excl = 0, j = t - 1;
@@ -51,7 +52,7 @@ __device__ __forceinline__ long long look_back_resolve(unsigned long long *tstat
         const int stop = m2 ? __ffs(m2) - 1 : 31;
         const unsigned int need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
         if (m0 & need) {
-            if (++spins > LOOKBACK_SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 timed_out = true;
                 break;
             }

@@ -379,7 +379,7 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 template <int DIM, int PASS, class C, int K>
 __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase,
                                           const int (&p)[K], const bool (&v)[K], int &cnt, float &acc, int *col,
-                                          long long rp, unsigned int &n32, unsigned int &n64) {
+                                          long long rp, unsigned int &n32, unsigned int &n64, bool dens) {
     const int lane = threadIdx.x & 31;
     float r2[K];
     int jj[K];
@@ -414,7 +414,7 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
 #pragma unroll
         for (int k = 0; k < K; ++k)
             if (in[k]) col[rp + cnt++] = jj[k];
-    } else {
+    } else if (dens) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
@@ -428,7 +428,7 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
 template <int DIM, int PASS, class C>
 __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase, int nwin,
                                             unsigned int nem, int &cnt, float &acc, int *col, long long rp,
-                                            unsigned int &n32, unsigned int &n64) {
+                                            unsigned int &n32, unsigned int &n64, bool dens) {
     const int lane = threadIdx.x & 31;
     BitCursor cur;
     cur.nem = nem;
@@ -437,7 +437,7 @@ __device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, co
         bool v[C::WB];
         next_bits<C::WB, C>(S, lane, wbase, cur, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
-        walk_bits<DIM, PASS, C, C::WB>(S, g, h, wbase, p, v, cnt, acc, col, rp, n32, n64);
+        walk_bits<DIM, PASS, C, C::WB>(S, g, h, wbase, p, v, cnt, acc, col, rp, n32, n64, dens);
     }
     if (PASS == PASS_COUNT) {
         // the neighbours of this window: its bits that survived the re-decision
@@ -483,7 +483,8 @@ __device__ __forceinline__ void group_setup(TileSmem<C> &S, const GridDev &g, Ho
 template <int DIM, int PASS, class C>
 __device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home &h, bool act, const Group &G,
                                           float cullT, int &cnt, float &acc, int *col, long long rp,
-                                          unsigned int &n32, unsigned int &n64, int &kept_out, int p0, int nhome) {
+                                          unsigned int &n32, unsigned int &n64, int &kept_out, int p0, int nhome,
+                                          bool dens) {
     const int lane = threadIdx.x & 31;
     int cur = 0, passes = 0, kept = 0;
     while (true) {
@@ -496,7 +497,7 @@ __device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home
             const int nwin = (wc + 31) >> 5;
             const int self_slot = (sp >= w0 && sp < w0 + wc) ? sp - w0 : -1;
             const unsigned int nem = test_window<DIM, C>(S, h, act, g.neg_t16, G.tau, w0 >> 5, nwin, self_slot);
-            walk_window<DIM, PASS, C>(S, g, h, w0 >> 5, nwin, nem, cnt, acc, col, rp, n32, n64);
+            walk_window<DIM, PASS, C>(S, g, h, w0 >> 5, nwin, nem, cnt, acc, col, rp, n32, n64, dens);
         }
         constexpr int NROWS = DIM == 3 ? 9 : 3;
         if (cur >= S.rcum[NROWS]) break;
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
             Group G;
             group_setup<DIM, C>(S, g, h, act, cy, cz, gs, ge, G);
             simple &= run_group<DIM, PASS_COUNT, C>(S, g, h, act, G, cullT, cnt, acc, nullptr, 0, n32, n64, kept, p0,
-                                                 cnt_home);
+                                                 cnt_home, want_rho);
             ++groups;
             gs = ge;
         }
@@ -606,7 +607,8 @@ __global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
         unsigned short *stg = reinterpret_cast<unsigned short *>(&S.code[0]);
         const bool staged = simple && col != nullptr && agg <= stg_slots;
         if (staged) emit_bits<C>(S, lane, mine ? (kept + 31) >> 5 : 0, rstart, stg, nullptr, nullptr);
-        const long long pre = look_back_resolve(tstate, t, agg, &g0.status->flags);
+        const long long pre =
+            look_back_resolve(tstate, t, agg, &g0.status->flags, g0.spin_limit > 0 ? g0.spin_limit : LOOKBACK_SPIN_LIMIT);
         const bool wc = col != nullptr && pre + agg <= cap;
         if (col != nullptr && !wc && lane == 0) atomicOr(&g0.status->flags, ST_CAPACITY);
         if (mine) {
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
                 group_setup<DIM, C>(S, g, h, act, cy, cz, gs, ge, G);
                 int kk;
                 run_group<DIM, PASS_EMIT, C>(S, g, h, act, G, cullT, ecnt, dummy, col, pre + rstart, e32, e64, kk, p0,
-                                          cnt_home);
+                                          cnt_home, false);
                 gs = ge;
             }
         }
@@ -772,12 +774,6 @@ __global__ void __launch_bounds__(ROWTILE_NT) k_row_tiles_lb(GridDev g, long lon
     }
 }
 
-// Cell x of every sorted particle.
-__global__ void k_cell_x(GridDev g, const int *__restrict__ scell, int *__restrict__ sx) {
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += (long long)gridDim.x * blockDim.x)
-        sx[s] = scell[s] % g.nk[0];
-}
-
 // The staged output area (code, pw, f32, then the launch's extra dynamic
 // shared memory) must be one contiguous range.
 template <class C>
@@ -837,24 +833,16 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
 }  // namespace
 
 // Build the tile list of a binned grid.  tcount: int[nrow], toff: int64[nrow+1],
-// tiles: int4[ntiles_max] with ntiles_max = n / 32 + nrow.  cstate != nullptr:
-// one launch with a look-back over chunks of rows (cstate: nrow + 1 zeroed
+// tiles: int4[ntiles_max].  span_limited: tiles of at most TW particles within
+// TILE_SPAN cells (ntiles_max = tiles_max(n, ncell, nrow)), else plain runs of
+// TW particles of a row (ntiles_max = n / TW + nrow + 1: the bound the
+// no-allocation search sizes its fixed scratch for).  cstate != nullptr: one
+// launch with a look-back over chunks of rows (cstate: nrow + 1 zeroed
 // entries; tcount and scan_tmp unused), else count, scan and write.
-cudaError_t launch_tiles(const GridDev &g, const int *scell, int *scell_x, bool need_cell_x, int *tcount,
-                         long long *toff, void *scan_tmp, int4 *tiles, unsigned long long *cstate, int sm_count,
-                         cudaStream_t s) {
-    // the no-allocation path (need_cell_x) keeps plain runs of TW particles
-    const bool span_limited = !need_cell_x;
+cudaError_t launch_tiles(const GridDev &g, bool span_limited, int *tcount, long long *toff, void *scan_tmp,
+                         int4 *tiles, unsigned long long *cstate, int sm_count, cudaStream_t s) {
     const long long nrow = (long long)g.nk[1] * g.nk[2];
-    const int nt = 256;
-    long long bn = (g.n + nt - 1) / nt;
-    if (bn > (long long)sm_count * 16) bn = (long long)sm_count * 16;
-    if (bn < 1) bn = 1;
     ProfScope ps(TAG_SCAN, s);
-    if (need_cell_x) {
-        note_launch(1);
-        k_cell_x<<<(unsigned)bn, nt, 0, s>>>(g, scell, scell_x);
-    }
     const int nx = g.nk[0];
     const long long rpc = nx + 1 <= ROWTILE_SMEM_INTS ? std::min<long long>(ROWTILE_NT, (ROWTILE_SMEM_INTS - 1) / nx)
                                                       : ROWTILE_NT;
@@ -902,6 +890,21 @@ cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *
 // tile of 32 rows (with 15% to spare) needs more than 1.5 times the built-in
 // area: measured on 1M and 8M particle sets, the occupancy it costs
 // outweighs the coalesced output for the tiles just above the area.
+TileLaunch tile_choose_grid(double last_nbr, long long n, long long ncell, int dim, double kh, double hc,
+                            int tile_shape, int staging) {
+    // neighbours per particle: the last measured value, else the
+    // uniform-density estimate (particles per cell x the search sphere's
+    // volume in cells)
+    double nbr = last_nbr;
+    if (nbr <= 0) {
+        const double ppc = (double)n / (double)(ncell > 0 ? ncell : 1), r = kh / hc;
+        nbr = dim == 3 ? ppc * 4.18879 * r * r * r : ppc * 3.14159 * r * r;
+    }
+    TileLaunch tv = tile_choose(nbr, tile_shape);
+    if (staging >= 0) tv.extra = staging;
+    return tv;
+}
+
 TileLaunch tile_choose(double nbr, int shape) {
     TileLaunch v;
     const double sparse_slots = (double)TileSmem<TileSparse>::staging_bytes() / 2.0;

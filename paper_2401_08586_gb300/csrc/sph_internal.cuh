@@ -70,6 +70,7 @@ struct GridDev {
     double w_norm64;      // FP64-CLL mode: m * alpha_d
     double w_self64;
     DevStatus *status;
+    int spin_limit;       // polls before a look-back wait gives up (0: LOOKBACK_SPIN_LIMIT)
 };
 
 // Cell coordinates of a linear cell id (c = (cz ny + cy) nx + cx).
@@ -217,10 +218,12 @@ struct GridView {
     int order;
     long long n;
     long long nrow;    // rows of cells along x: nk[1] * nk[2]
+    int tile_shape;    // tile-search shape and extra staging the grid's own query would use
+    int tile_extra;
 };
 int grid_view(sph_grid_t grid, GridView *v);
 int set_error(int code, const char *msg);
-void reset_counters_async(DevStatus *st, cudaStream_t s);
+cudaError_t reset_counters_async(DevStatus *st, cudaStream_t s);
 
 // ---- launch helpers (implemented in scan.cu / sort.cu) --------------------
 

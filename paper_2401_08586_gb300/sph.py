@@ -193,6 +193,7 @@ def sph_nnps_query_static(grid, row_ptr, col, col_capacity, rho=None, stream=Non
 SPH_OPT_FUSED = 1
 SPH_OPT_STAGING = 2
 SPH_OPT_TILE_SHAPE = 3
+SPH_OPT_TEST_LOOKBACK = 4
 
 
 def sph_grid_set_option(grid, option, value):

@@ -7,8 +7,11 @@ memory in a fixed array inside the library instead of allocating.
 Checked here through the C ABI: on two calls in a row, and after a call on
 another grid (the shared array keeps the previous call's contents), it gives
 the same CSR and density as sph_nnps_query on the same grid; sizes above its
-limit are refused with a clear error.  This file is named so that pytest
-collects it last.
+limit are refused with a clear error.  At its limits: a set of about 2^20
+particles with more than 16,384 rows of cells (the multi-block row scan inside
+the fixed array), a col_capacity below nnz (SPH_ERR_CAPACITY from the next
+sph_grid_check, nothing written past the capacity), and a grid of more than
+65,536 rows (refused).  This file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -89,4 +92,60 @@ def test_static_query_refuses_oversized_grids(sph):
     with pytest.raises(sph.SphError) as ei:
         sph.sph_nnps_query_static(g.handle, rp, col, 16)
     assert ei.value.code == sph.SPH_ERR_INVALID
+    g.close()
+
+
+def thin_slab(n, seed):
+    """Uniform random particles in a 0.05 x 1.5 x 1.5 slab: with kh = 0.01 the
+    grid has 5 x 150 x 150 cells, i.e. 22,500 rows of cells."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.0, size=(n, 3)) * np.array([0.05, 1.5, 1.5])
+
+
+def test_static_query_near_its_limits(sph):
+    n = (1 << 20) - 7
+    xyz = thin_slab(n, 21)
+    g = sph.Grid(torch.from_numpy(xyz).cuda(), 0.005, 0.01)
+    info = g.info()
+    assert int(info.nk[1]) * int(info.nk[2]) > 16384
+    ref = regular(sph, g)
+    cap = int(ref[0][-1])
+    same(static_call(sph, g, cap), ref)
+    same(static_call(sph, g, cap), ref)
+    g.close()
+
+
+def test_static_query_capacity_below_nnz(sph):
+    ps = W.c2_3d_1m(side=30)
+    g = sph.Grid(torch.from_numpy(ps.xyz).cuda(), ps.h, ps.kh)
+    ref = regular(sph, g)
+    nnz = int(ref[0][-1])
+    cap = nnz // 2
+    rp = torch.empty(g.n + 1, dtype=torch.int64, device="cuda")
+    col = torch.full((nnz + 1024,), -7, dtype=torch.int32, device="cuda")
+    sph.sph_nnps_query_static(g.handle, rp, col, cap)
+    torch.cuda.synchronize()
+    with pytest.raises(sph.SphError) as ei:
+        sph.sph_grid_check(g.handle)
+    assert ei.value.code == sph.SPH_ERR_CAPACITY
+    assert np.all(col[cap:].cpu().numpy() == -7)
+    # row pointers are complete even when the columns do not fit
+    assert np.array_equal(rp.cpu().numpy(), ref[0])
+    # and a call with enough room afterwards is exact
+    same(static_call(sph, g, nnz), ref)
+    g.close()
+
+
+def test_static_query_refuses_too_many_rows(sph):
+    rng = np.random.default_rng(5)
+    xyz = rng.uniform(0.0, 1.0, size=(20000, 3)) * np.array([0.05, 2.6, 2.6])  # 260 x 260 rows of cells
+    g = sph.Grid(torch.from_numpy(xyz).cuda(), 0.005, 0.01)
+    info = g.info()
+    assert int(info.nk[1]) * int(info.nk[2]) > 65536
+    rp = torch.empty(g.n + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(sph.SphError) as ei:
+        sph.sph_nnps_query_static(g.handle, rp, col, 16)
+    assert ei.value.code == sph.SPH_ERR_INVALID
+    assert "65536" in str(ei.value)
     g.close()
