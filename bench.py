@@ -81,7 +81,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("nnps_tile.cu", "nnps_common.cuh", "sph_internal.cuh", "lookback.cuh", "fastdiv.h"):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2401_08586_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -103,9 +103,13 @@ def ncu_traffic(workload_name, kernel_tag, key="bytes_per_launch"):
         return None
 
 
-# Instruction issue of GB300: 152 SMs x 4 schedulers, one warp instruction
-# per scheduler per clock.
-ISSUE_PER_CLOCK = 152 * 4
+KERNEL_SOURCES = ("nnps_tile.cu", "nnps_common.cuh", "sph_internal.cuh", "lookback.cuh", "fastdiv.h", "tile_rows.cuh")
+
+
+def issue_per_clock(sm_count):
+    """Warp instructions a device can issue per clock: 4 schedulers per SM,
+    one warp instruction each (Blackwell SM)."""
+    return 4 * sm_count
 
 
 class ClockSampler:
@@ -394,11 +398,13 @@ def main():
     inst = None if inst is None else inst * per_m
     issue = None
     if inst is not None and clocks.get("sm_mhz"):
-        ipeak = ISSUE_PER_CLOCK * clocks["sm_mhz"] * 1e6
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ipeak = issue_per_clock(sms) * clocks["sm_mhz"] * 1e6
         ia = inst / (dom_ms * 1e-3)
         issue = {"bound": "issue", "kernel": roofline["kernel"], "achieved": ia, "peak": ipeak,
                  "unit": "warp-instructions/s", "frac": ia / ipeak, "inst_per_launch": inst,
-                 "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction/clock x sampled SM clock"}
+                 "peak_source": "%d SMs (device properties) x 4 schedulers x 1 warp-instruction/clock x "
+                                "sampled SM clock" % sms}
     # whole path: binning 56 B/particle, search + fused density 36 B/particle + 4 B/neighbour
     alg_step = n * (56 + 36) + 4 * nnz
     step_ms_mean = 1e3 * dev_total_s / args.steps
@@ -422,8 +428,10 @@ def main():
         "fp16_rejected_in_fp32": info.stat_fp32_pairs, "fp64_tier_pairs": info.stat_fp64_pairs,
     }
     if not args.no_extras:
-        line["fp64_cll"] = bench_fp64(sph, ps, xyz, dev, stream, max(3, args.steps // 4), value)
+        line["fp64_cll"] = bench_fp64(sph, ps, xyz, dev, stream, max(3, args.steps // 4), value,
+                                      line.get("roofline", {}).get("launch_ms"))
         line["fp64_cll"]["device_fp64_fma_tflops"] = sph.sph_device_fp64_rate() / 1e12
+        line["query_variants"] = bench_query_variants(sph, ps, xyz, dev, stream, max(3, min(args.steps, 20)))
         line["e2e"] = bench_e2e(sph, ps, dev, stream, args)
         if world > 1:
             line["e2e"]["value"] = world * n * args.steps / replicas.max_over_ranks(line["e2e"]["seconds"], world,
@@ -442,8 +450,11 @@ def main():
     return 0
 
 
-def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value):
-    """The FP64 cell link-list on the same GPU, same binning and CSR."""
+def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value, fp16_search_ms=None):
+    """The FP64 cell link-list on the same GPU, same binning and CSR: the tile
+    search with the FP64 test and FP64 density (the same kernel structure as
+    the FP16-RCLL search, so the ratio is one of precision), and, as a second
+    figure, the two-pass CTA-per-cell FP64 search."""
     import torch
     n = ps.n
     sptr = stream.cuda_stream
@@ -459,22 +470,95 @@ def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value):
         sph.sph_bin_cells(params, xyz, n, sptr, g)
         sph.sph_nnps_query(g, rp, col, col.numel(), False, rho, sptr)
 
-    step()
-    torch.cuda.synchronize()
-    ms = []
-    for k in range(steps):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+    def timed(k_steps):
         step()
-        b.record(stream)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(k_steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / k_steps
+
+    sph.sph_profile_reset()
+    sph.sph_profile_select("fused")
+    sph.sph_profile_enable(True)
+    t_tile = timed(steps)
+    sph.sph_profile_enable(False)
+    fms, fc = sph.sph_profile_read("fused")
+    search_ms = fms / fc if fc else None
+    sph.sph_grid_set_option(g, sph.SPH_OPT_FUSED, 0)
+    t_two = timed(max(2, steps // 3))
     sph.sph_grid_check(g, sptr)
     sph.sph_grid_free(g)
-    v = n * steps / (sum(ms) / 1e3)
-    return {"value": v, "unit": "particles/s", "ms_per_step": sum(ms) / steps, "steps": steps,
-            "fp16_rcll_speedup": fp16_value / v}
+    v = n / (t_tile / 1e3)
+    out = {"value": v, "unit": "particles/s", "ms_per_step": t_tile, "steps": steps,
+           "search": "single-pass tile search, FP64 test and FP64 density (same tiles, cull, look-back, CSR)",
+           "search_ms": search_ms, "fp16_rcll_speedup": fp16_value / v,
+           "two_pass_ms_per_step": t_two,
+           "two_pass_note": "FP64 two-pass search, one thread block per cell (the earlier baseline)"}
+    if fp16_search_ms and search_ms:
+        out["search_speedup"] = search_ms / fp16_search_ms
+    return out
+
+
+def bench_query_variants(sph, ps, xyz, dev, stream, steps):
+    """The search's other query forms on the same workload, each through the
+    tile search: count only (col == NULL: row pointers and nnz, the capacity
+    discovery) and canonical order (input-order rows, input-index columns
+    ascending: cell-order search, then row permutation and per-row sort).
+    CUDA events around each call; the canonical query reads nnz back to the
+    host inside the call, so its figure includes that round trip, and the
+    library's kernel times are given beside it."""
+    import torch
+    n = ps.n
+    sptr = stream.cuda_stream
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+
+    def events(fn, k_steps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(k_steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / k_steps
+
+    params = sph.make_params(ps.dim, ps.h, ps.kh, order=sph.SPH_ORDER_CELL)
+    g = sph.sph_bin_cells(params, xyz, n, sptr, None)
+    out["count_only_ms"] = events(lambda: sph.sph_nnps_query(g, rp, None, 0, False, None, sptr), steps)
+    sph.sph_grid_free(g)
+
+    params = sph.make_params(ps.dim, ps.h, ps.kh, order=sph.SPH_ORDER_CANONICAL)
+    g = sph.sph_bin_cells(params, xyz, n, sptr, None)
+    nnz = sph.sph_nnps_query(g, rp, None, 0, True, None, sptr)
+    col = torch.empty(nnz + 1024, dtype=torch.int32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    sph.sph_profile_reset()
+    sph.sph_profile_select(None)
+    sph.sph_profile_enable(True)
+    out["canonical_ms"] = events(lambda: sph.sph_nnps_query(g, rp, col, col.numel(), False, rho, sptr), steps)
+    sph.sph_profile_enable(False)
+    kern = {}
+    for tag in ("scan", "fused", "canon", "sort"):
+        ms, c = sph.sph_profile_read(tag)
+        if c:
+            kern[tag] = ms / (steps + 1)
+    out["canonical_kernel_ms"] = kern
+    sph.sph_grid_check(g, sptr)
+    sph.sph_grid_free(g)
+    return out
 
 
 def bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, steps):

@@ -249,12 +249,17 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
                           void *stream);
 
 /* Per-grid switches (host call, no GPU work).
- *   SPH_OPT_FUSED selects the search of cell-order FP16-RCLL queries with
- *     col != NULL (all give identical results):
+ *   SPH_OPT_FUSED selects the search (all give identical neighbour lists):
  *       1 (default) single pass, one warp per 32-particle tile of a row of
- *         cells, CSR offsets found by a look-back across tiles;
- *       2 single pass, one thread block per cell, look-back across cells;
- *       0 two passes (count pass, row scan, fill pass). */
+ *         cells, CSR offsets found by a look-back across tiles; every query
+ *         (count only, cell or canonical order) of either precision: FP16
+ *         test with FP32/FP64 re-decision on FP16-RCLL grids, the FP64 test
+ *         and FP64 density on FP64-CLL grids;
+ *       2 single pass, one thread block per cell, look-back across cells
+ *         (cell-order FP16-RCLL queries with col != NULL; other queries take
+ *         two passes);
+ *       0 two passes (count pass, row scan, fill pass), one thread block per
+ *         cell. */
 #define SPH_OPT_FUSED 1
 /*   SPH_OPT_STAGING: bytes of shared memory the tile search (SPH_OPT_FUSED 1)
  *     adds to its output staging area: -1 (default) sizes it from the

@@ -280,8 +280,9 @@ extern "C" int sph_advance(sph_grid_t grid, const double *xyz_new, const double 
 }
 
 // Single pass, one warp per 32-particle row tile, look-back across tiles
-// (nnps_tile.cu), in cell order: row pointers always; columns and the fused
-// density when col / rho are given (col == NULL: the count only).
+// (nnps_tile.cu; FP64 grids: nnps_tile64.cu), in cell order: row pointers
+// always; columns and the fused density when col / rho are given (col ==
+// NULL: the count only).
 static int run_tile_search(sph_grid_s *g, long long *rp_cell, int *col, long long cap, float *rho, bool test_lb,
                            cudaStream_t s) {
     const long long n = g->n;
@@ -300,6 +301,11 @@ static int run_tile_search(sph_grid_s *g, long long *rp_cell, int *col, long lon
     if (test_lb) d.spin_limit = g->test_lookback;
     SPH_CUDA(launch_tiles(d, true, P<int>(g->tcount), P<long long>(g->toff), g->scan_tmp.p, P<int4>(g->tiles),
                           tstate + ntiles_max, g->sm_count, s));
+    if (g->p.precision == SPH_PREC_FP64_CLL) {
+        SPH_CUDA(launch_nnps_tile64(d, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell, col, cap,
+                                    rho, tstate, g->sm_count, s));
+        return SPH_OK;
+    }
     const TileLaunch tv =
         tile_choose_grid(g->last_nbr, n, g->ncell, g->p.dim, g->p.kh, g->hc, g->tile_shape, g->staging);
     SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell, col,
@@ -340,10 +346,11 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
     SPH_TRY(ensure(g->rowcnt, n * sizeof(int), s));
     const bool canonical = g->p.order == SPH_ORDER_CANONICAL;
     const int prec = g->p.precision;
-    // the single-pass tile search serves every FP16-RCLL query unless another
-    // search variant is asked for (SPH_OPT_FUSED 0: two passes; 2: one CTA per
-    // cell, cell-order queries with columns only)
-    const bool tile = prec == SPH_PREC_FP16_RCLL && (g->fused_enabled == 1 || test_lb);
+    // the single-pass tile search (FP16-RCLL, or its FP64 form on FP64-CLL
+    // grids) serves every query unless another search variant is asked for
+    // (SPH_OPT_FUSED 0: two passes; 2: one CTA per cell, FP16 cell-order
+    // queries with columns only; other FP64 queries then take two passes)
+    const bool tile = g->fused_enabled == 1 || test_lb;
     long long *rp_cell = reinterpret_cast<long long *>(row_ptr);
     if (canonical) {
         SPH_TRY(ensure(g->tmp_rp, (n + 1) * sizeof(long long), s));

@@ -315,7 +315,7 @@ static cudaError_t batch_prep(sph_batch_s *b, int nsys, int dim, long long ntot,
                             b->sm_count, s)) != cudaSuccess)
         return e;
     if ((e = segmented_sort_i32(P<int>(b->orig_g), P<int>(b->cell_start), ncell, P<int>(b->big_list),
-                                &st->big_cells, s)) != cudaSuccess)
+                                &st->big_cells, b->sm_count, s)) != cudaSuccess)
         return e;
     {
         ProfScope ps(TAG_CONVERT, s);

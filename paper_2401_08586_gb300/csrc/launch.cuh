@@ -87,6 +87,11 @@ struct TileLaunch {
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
                              unsigned long long *tstate, TileLaunch v, bool zeroed, int sm_count, cudaStream_t s);
+// The same search with the FP64 test and density on the cell-ordered FP64
+// coordinates (SPH_PREC_FP64_CLL grids; nnps_tile64.cu); tstate zeroed.
+cudaError_t launch_nnps_tile64(const GridDev &g, const int4 *tiles, const long long *ntiles_dev,
+                               long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
+                               unsigned long long *tstate, int sm_count, cudaStream_t s);
 // Shape (shape < 0: chosen from nbr) and staging for about nbr neighbours per particle.
 TileLaunch tile_choose(double neighbours_per_particle, int shape);
 // The same for a grid: its last measured neighbours per particle (else the

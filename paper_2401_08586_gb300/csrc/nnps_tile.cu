@@ -38,6 +38,7 @@
 #include "launch.cuh"
 #include "lookback.cuh"
 #include "nnps_common.cuh"
+#include "tile_rows.cuh"
 
 namespace sph {
 
@@ -144,46 +145,10 @@ struct Group {
     unsigned int tau;              // FP16 band (half2 bits)
 };
 
-// Candidate row table of a group: for each of the 3^d rows of cells around
-// the group's row (cy, cz), the sorted range of cells [xlo, xhi].
+// Candidate row table of a group (tile_rows.cuh).
 template <int DIM, class C>
 __device__ __forceinline__ void group_rows(TileSmem<C> &S, const GridDev &g, int cy, int cz, const Group &G) {
-    constexpr int NROWS = DIM == 3 ? 9 : 3;
-    const int lane = threadIdx.x & 31;
-    const int nx = g.nk[0], ny = g.nk[1], nz = g.nk[2];
-    // lane 2r + e loads the start (e = 0) or end (e = 1) of row r
-    int v = -1;
-    const int r = lane >> 1, e = lane & 1;
-    if (r < NROWS) {
-        const int dy = DIM == 3 ? (r % 3) - 1 : r - 1;
-        const int dz = DIM == 3 ? (r / 3) - 1 : 0;
-        const int yy = cy + dy, zz = cz + dz;
-        if (yy >= 0 && yy < ny && zz >= 0 && zz < nz)
-            v = g.cell_start[((long long)zz * ny + yy) * nx + (e ? G.xhi + 1 : G.xlo)];
-    }
-    const int vend = __shfl_down_sync(0xffffffffu, v, 1);
-    const int mylen = (e == 0 && v >= 0) ? vend - v : 0;
-    // rows to lanes 0 .. NROWS-1: start and length
-    const int src = 2 * (lane < NROWS ? lane : 0);
-    const int st = __shfl_sync(0xffffffffu, v, src);
-    int len = __shfl_sync(0xffffffffu, mylen, src);
-    if (lane >= NROWS) len = 0;
-    // flat index of the candidates: rcum[r] = candidates in rows before r
-    int inc = len;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const int up = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += up;
-    }
-    if (lane < NROWS) {
-        const int dy = DIM == 3 ? (lane % 3) - 1 : lane - 1;
-        const int dz = DIM == 3 ? (lane / 3) - 1 : 0;
-        S.rt[lane] = make_int4((st >= 0 ? st : 0) - (inc - len), ((dy + 1) << 3) | ((dz + 1) << 5),
-                               __float_as_int(2.f * (float)dy), __float_as_int(2.f * (float)dz));
-        S.rcum[lane + 1] = inc;
-    }
-    if (lane == 0) S.rcum[0] = 0;
-    __syncwarp();
+    tile_candidate_rows<DIM>(S.rt, S.rcum, g, cy, cz, G.xlo, G.xhi);
 }
 
 constexpr int CULL_CHUNKS = 4;  // chunks of 32 candidates whose loads are in flight together

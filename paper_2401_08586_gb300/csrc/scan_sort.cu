@@ -271,15 +271,15 @@ __global__ void __launch_bounds__(SORT_NT) k_seg_sort_big(int *keys, const IdxT 
 
 template <typename IdxT>
 cudaError_t seg_sort_impl(int *keys, const IdxT *seg, long long nseg, int *big_list,
-                          unsigned int *big_count, cudaStream_t s) {
+                          unsigned int *big_count, int sm_count, cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
     ProfScope ps(TAG_SORT, s);
     note_launch(2);
     cudaMemsetAsync(big_count, 0, sizeof(unsigned int), s);
     long long blocks = (nseg * 32 + SORT_NT - 1) / SORT_NT;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
     k_seg_sort_small<IdxT><<<(unsigned)blocks, SORT_NT, 0, s>>>(keys, seg, nseg, big_list, big_count);
-    k_seg_sort_big<IdxT><<<152, SORT_NT, 0, s>>>(keys, seg, big_list, big_count);
+    k_seg_sort_big<IdxT><<<(unsigned)sm_count, SORT_NT, 0, s>>>(keys, seg, big_list, big_count);
     return cudaGetLastError();
 }
 
@@ -314,13 +314,13 @@ cudaError_t exclusive_scan_i64(const int *in, long long *out, long long n, void 
 }
 
 cudaError_t segmented_sort_i32(int *keys, const int *seg_start, long long nseg, int *big_list,
-                               unsigned int *big_count, cudaStream_t s) {
-    return seg_sort_impl<int>(keys, seg_start, nseg, big_list, big_count, s);
+                               unsigned int *big_count, int sm_count, cudaStream_t s) {
+    return seg_sort_impl<int>(keys, seg_start, nseg, big_list, big_count, sm_count, s);
 }
 
 cudaError_t segmented_sort_rows(int *keys, const long long *row_ptr, long long nrows,
-                                int *big_list, unsigned int *big_count, cudaStream_t s) {
-    return seg_sort_impl<long long>(keys, row_ptr, nrows, big_list, big_count, s);
+                                int *big_list, unsigned int *big_count, int sm_count, cudaStream_t s) {
+    return seg_sort_impl<long long>(keys, row_ptr, nrows, big_list, big_count, sm_count, s);
 }
 
 }  // namespace sph

@@ -191,7 +191,7 @@ cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long 
     k_canon_copy<<<(unsigned)wblocks, nt, 0, s>>>(n, rank, orig_id, rp_cell, col_cell, rho_cell, rp, col,
                                                    rho, col != nullptr);
     if (col != nullptr) {
-        e = segmented_sort_rows(col, rp, n, big_list, big_count, s);
+        e = segmented_sort_rows(col, rp, n, big_list, big_count, sm_count, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

@@ -255,9 +255,9 @@ inline unsigned long long *cnt_scan_state(int *cnt, long long ncell) {
 // c < nseg.  Segments longer than 32 are listed in big_list (capacity nseg)
 // with their count in *big_count (device) and sorted by a block-level pass.
 cudaError_t segmented_sort_i32(int *keys, const int *seg_start, long long nseg, int *big_list,
-                               unsigned int *big_count, cudaStream_t s);
+                               unsigned int *big_count, int sm_count, cudaStream_t s);
 // Same for int64-delimited segments (CSR rows).
 cudaError_t segmented_sort_rows(int *keys, const long long *row_ptr, long long nrows,
-                                int *big_list, unsigned int *big_count, cudaStream_t s);
+                                int *big_list, unsigned int *big_count, int sm_count, cudaStream_t s);
 
 }  // namespace sph

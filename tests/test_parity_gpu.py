@@ -93,8 +93,8 @@ CASES = {
 }
 
 
-VARIANTS = [(0, 1), (0, 2), (0, 0), (1, 0)]
-VARIANT_IDS = ["cell-tile", "cell-cta", "cell-twopass", "canonical"]
+VARIANTS = [(0, 1), (0, 2), (0, 0), (1, 1), (1, 0)]
+VARIANT_IDS = ["cell-tile", "cell-cta", "cell-twopass", "canonical-tile", "canonical-twopass"]
 
 
 @pytest.mark.parametrize("order,fused", VARIANTS, ids=VARIANT_IDS)
@@ -106,11 +106,33 @@ def test_parity_fp16_rcll(sph, case, order, fused):
     assert sph.sph_grid_check(out["grid"].handle) == 0
 
 
-@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "faces3d", "circle3d_1e-12", "dambreak_small"])
-def test_parity_fp64_cll(sph, case):
+FP64_VARIANTS = [(0, 1), (1, 1), (1, 0)]
+FP64_VARIANT_IDS = ["cell-tile", "canonical-tile", "canonical-twopass"]
+
+
+@pytest.mark.parametrize("order,fused", FP64_VARIANTS, ids=FP64_VARIANT_IDS)
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "faces3d", "circle3d_1e-12", "dambreak_small",
+                                  "random2d", "line", "one", "two"])
+def test_parity_fp64_cll(sph, case, order, fused):
+    """The FP64 cell link-list (the FP64 tile search by default, the two-pass
+    search with SPH_OPT_FUSED 0): the oracle's CSR bit for bit, density within
+    the FP32 output's tolerance."""
     xyz, h = CASES[case]()
-    out = run(sph, xyz, h, 2 * h, 1, precision=sph.SPH_PREC_FP64_CLL)
-    check_against_oracle(out, xyz, h, 2 * h, 1)
+    out = run(sph, xyz, h, 2 * h, order, precision=sph.SPH_PREC_FP64_CLL, fused=fused)
+    check_against_oracle(out, xyz, h, 2 * h, order)
+    assert sph.sph_grid_check(out["grid"].handle) == 0
+
+
+def test_fp64_tile_ties_and_count_only(sph):
+    """Exact ties at kh (power-of-two lattice) are excluded by the FP64 tile
+    search's strict test; its count-only query gives the same row pointers."""
+    dx = 1.0 / 256
+    xyz = W.exact_lattice(14, 3, dx)
+    out = run(sph, xyz, 1.5 * dx, 3 * dx, 0, precision=sph.SPH_PREC_FP64_CLL)
+    check_against_oracle(out, xyz, 1.5 * dx, 3 * dx, 0)
+    rp = torch.empty(xyz.shape[0] + 1, dtype=torch.int64, device="cuda")
+    nnz = sph.sph_nnps_query(out["grid"].handle, rp, None, 0, True, None)
+    assert nnz == out["rp"][-1] and np.array_equal(rp.cpu().numpy(), out["rp"])
 
 
 def test_exact_ties_power_of_two_lattice(sph):
