@@ -440,7 +440,7 @@ def main():
         line["gradient_a5"] = bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, args.steps)
         line["density_half"] = bench_density_half(sph, ps, grid, dev, stream, args.steps)
         line["timestep"] = bench_timestep(sph, ps, xyz, dev, stream, row_ptr, col, cap, rho, args.steps)
-        line["serving"] = bench_serve(sph, dev, count=450, warm=50)
+        line["serving"] = bench_serve(sph, dev, count=2000, warm=200)
         if world == 1 and rank == 0:
             line["cpu_baseline"] = cpu_baseline(ps)
     sph.sph_grid_free(grid)

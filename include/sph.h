@@ -286,6 +286,12 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *     sph_grid_check does) and the GPU context stays usable.  Set 0 to go
  *     back to normal queries. */
 #define SPH_OPT_TEST_LOOKBACK 4
+/*   SPH_OPT_SM_SHARE: percent (1 .. 100, default 100) of the device's resident
+ *     thread-block slots the tile search's persistent grid takes.  Below 100
+ *     the search leaves room for kernels of other streams to run beside it
+ *     (the request server gives large requests a share so that small ones
+ *     are not queued behind them); results are unchanged. */
+#define SPH_OPT_SM_SHARE 5
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 
 /* Fill *info (host) with the grid's sizes and device pointers.  The pointers
@@ -451,6 +457,13 @@ int sph_batch_free(sph_batch_t batch);
  * are searched as one batch (up to max_batch requests) and their results
  * split afterwards (continuous batching).  A request that fails (for example
  * a non-finite coordinate) reports its error alone; the others are unaffected.
+ * Requests of more than large_n particles run on a low-priority stream and
+ * their persistent search takes only large_sm_percent of the GPU's resident
+ * thread-block slots; the others run on high-priority streams, so that small
+ * requests arriving next to a large one start at once instead of queueing
+ * behind it.  Unless reserve_pool is -1, the server grows the device's
+ * stream-ordered memory pool to the budget (or, failing that, as far as it
+ * can) once at creation, so that no request waits on the pool growing.
  * The paper serves no requests; this is the library's serving layer.
  */
 typedef struct sph_server_s *sph_server_t;
@@ -461,6 +474,9 @@ typedef struct {
     int32_t max_batch;        /* requests per batched search, 0: 64 */
     int64_t small_n;          /* batching threshold in particles, 0: 32768 */
     int64_t max_wait_ns;      /* passing limit, 0: 20 ms */
+    int64_t large_n;          /* requests above it run beside the others on a share of the GPU, 0: 262144 */
+    int32_t large_sm_percent; /* that share in percent (1 .. 100), 0: 75 */
+    int32_t reserve_pool;     /* 0: grow the memory pool to the budget at creation, -1: do not */
 } sph_server_cfg;
 
 typedef struct {

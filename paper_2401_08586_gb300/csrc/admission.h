@@ -34,6 +34,8 @@ struct SchedCfg {
     int64_t batch_max_n;   // particles per batch
     int max_batch;         // requests per batch
     int64_t max_wait_ns;   // a blocked request older than this is not passed
+    int64_t large_n = 262144;    // requests above it run on a low-priority stream on part of the GPU
+    int large_sm_percent = 75;   // the share of the GPU's resident thread blocks they take
 };
 
 // Device bytes held for a request of n particles: working arrays, the

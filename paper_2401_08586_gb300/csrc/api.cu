@@ -36,6 +36,7 @@ struct sph_grid_s {
     int tile_shape = -1;    // shared-memory shape of the tile search (SPH_OPT_TILE_SHAPE; -1: automatic)
     double last_nbr = 0;    // neighbours per particle of the last query whose nnz reached the host
     int test_lookback = 0;  // SPH_OPT_TEST_LOOKBACK: > 0 skips the first tile, waits give up after that many polls
+    int sm_percent = 100;   // SPH_OPT_SM_SHARE
     DevBuf rel64, rel64u;   // FP64 relative coordinates kept across time steps (cell / input order)
     DevBuf fsplit;          // gradient: the field as float hi + lo in cell order
     DevBuf study;           // precision study counters
@@ -306,8 +307,8 @@ static int run_tile_search(sph_grid_s *g, long long *rp_cell, int *col, long lon
                                     rho, tstate, g->sm_count, s));
         return SPH_OK;
     }
-    const TileLaunch tv =
-        tile_choose_grid(g->last_nbr, n, g->ncell, g->p.dim, g->p.kh, g->hc, g->tile_shape, g->staging);
+    const TileLaunch tv = tile_choose_grid(g->last_nbr, n, g->ncell, g->p.dim, g->p.kh, g->hc, g->tile_shape,
+                                           g->staging, g->sm_percent);
     SPH_CUDA(launch_nnps_tile(d, nullptr, P<int4>(g->tiles), P<long long>(g->toff) + nrow, ntiles_max, rp_cell, col,
                               cap, rho, tstate, tv, true, g->sm_count, s));
     return SPH_OK;
@@ -577,6 +578,11 @@ extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
     if (option == SPH_OPT_TILE_SHAPE) {
         if (value < -1 || value > 2) return fail(SPH_ERR_INVALID, "SPH_OPT_TILE_SHAPE takes -1, 0, 1 or 2");
         g->tile_shape = (int)value;
+        return SPH_OK;
+    }
+    if (option == SPH_OPT_SM_SHARE) {
+        if (value < 1 || value > 100) return fail(SPH_ERR_INVALID, "SPH_OPT_SM_SHARE takes 1 .. 100 (percent)");
+        g->sm_percent = (int)value;
         return SPH_OK;
     }
     if (option == SPH_OPT_TEST_LOOKBACK) {

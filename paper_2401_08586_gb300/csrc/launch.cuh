@@ -83,6 +83,7 @@ enum { TILE_SPARSE = 0, TILE_DENSE = 1 };
 struct TileLaunch {
     int shape;
     int extra;
+    int sm_percent = 100;  // share of the device's resident CTA slots the persistent grid takes (1 .. 100)
 };
 cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                              long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
@@ -97,6 +98,6 @@ TileLaunch tile_choose(double neighbours_per_particle, int shape);
 // The same for a grid: its last measured neighbours per particle (else the
 // uniform-density estimate) and its SPH_OPT_TILE_SHAPE / SPH_OPT_STAGING settings.
 TileLaunch tile_choose_grid(double last_nbr, long long n, long long ncell, int dim, double kh, double hc,
-                            int tile_shape, int staging);
+                            int tile_shape, int staging, int sm_percent = 100);
 
 }  // namespace sph

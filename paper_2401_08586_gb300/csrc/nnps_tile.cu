@@ -757,7 +757,8 @@ static_assert(fits_cta<TileSparse>() && fits_cta<TileDense>(), "shared memory pe
 template <class C>
 cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tiles, const long long *ntiles_dev,
                          long long ntiles_max, long long *row_ptr, int *col, long long cap, float *rho,
-                         unsigned long long *tstate, int extra_smem, bool zeroed, int sm_count, cudaStream_t s) {
+                         unsigned long long *tstate, int extra_smem, bool zeroed, int sm_count, int sm_percent,
+                         cudaStream_t s) {
     using SM = TileSmem<C>;
     extra_smem = (extra_smem + 15) & ~15;  // keeps every warp's area 16-byte aligned
     const size_t warp_bytes = sizeof(SM) + (size_t)extra_smem;
@@ -780,6 +781,9 @@ cudaError_t launch_shape(const GridDev &g, const GridDev *gsys, const int4 *tile
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * C::WPB, sb);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)sm_count * per_sm;
+    // a share below 100 % leaves resident slots for other streams' kernels
+    // (the request server's small requests next to a large one)
+    if (sm_percent > 0 && sm_percent < 100) blocks = (blocks * sm_percent + 99) / 100;
     if (blocks > (ntiles_max + C::WPB - 1) / C::WPB) blocks = (ntiles_max + C::WPB - 1) / C::WPB;
     if (blocks < 1) blocks = 1;
     if (!zeroed) {
@@ -842,9 +846,9 @@ cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *
         return cudaErrorInvalidValue;
     if (v.shape == TILE_DENSE)
         return launch_shape<TileDense>(g, gsys, tiles, ntiles_dev, ntiles_max, row_ptr, col, cap, rho, tstate,
-                                       v.extra, zeroed, sm_count, s);
+                                       v.extra, zeroed, sm_count, v.sm_percent, s);
     return launch_shape<TileSparse>(g, gsys, tiles, ntiles_dev, ntiles_max, row_ptr, col, cap, rho, tstate, v.extra,
-                                    zeroed, sm_count, s);
+                                    zeroed, sm_count, v.sm_percent, s);
 }
 
 // Shape and staging for a grid whose rows hold about `nbr` neighbours on
@@ -856,7 +860,7 @@ cudaError_t launch_nnps_tile(const GridDev &g, const GridDev *gsys, const int4 *
 // area: measured on 1M and 8M particle sets, the occupancy it costs
 // outweighs the coalesced output for the tiles just above the area.
 TileLaunch tile_choose_grid(double last_nbr, long long n, long long ncell, int dim, double kh, double hc,
-                            int tile_shape, int staging) {
+                            int tile_shape, int staging, int sm_percent) {
     // neighbours per particle: the last measured value, else the
     // uniform-density estimate (particles per cell x the search sphere's
     // volume in cells)
@@ -867,6 +871,7 @@ TileLaunch tile_choose_grid(double last_nbr, long long n, long long ncell, int d
     }
     TileLaunch tv = tile_choose(nbr, tile_shape);
     if (staging >= 0) tv.extra = staging;
+    tv.sm_percent = sm_percent;
     return tv;
 }
 

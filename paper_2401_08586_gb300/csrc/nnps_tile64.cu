@@ -17,7 +17,9 @@
 //   * test: r^2 = (dx0 dx0 + dx1 dx1) + dx2 dx2 evaluated exactly as the
 //     definition writes it (no contraction); neighbour iff r^2 < kh^2 and
 //     j != i: one bit per pair, the decision of the FP64 definition itself;
-//   * each lane walks its bits: density W(r / h) of Eq. 3 in FP64.
+//   * each lane walks its bits: density W(r / h) of Eq. 3 in FP64, with the
+//     kernel written without branches as 6 P(R) = (2 - R)^3 - 4 max(1 - R, 0)^3
+//     (the two pieces of Eq. 3 in one expression) and r = r^2 rsqrt(r^2).
 // The tile's row counts give its total; the CSR offset comes from the
 // decoupled look-back over earlier tiles; each lane writes its row pointer,
 // its density and its row from its bits.  A tile whose kept list needs more
@@ -133,6 +135,16 @@ __device__ __forceinline__ void stage64(Smem64 &S, const GridDev &g, int w0, int
     __syncwarp();
 }
 
+// 6 P(R) of Eq. 3 for 0 <= R < 2: (2 - R)^3 - 4 (1 - R)^3 on [0, 1) equals
+// 4 - 6 R^2 + 3 R^3 = 6 (2/3 - R^2 + R^3 / 2), and (2 - R)^3 alone on [1, 2).
+__device__ __forceinline__ double six_p64(double R) {
+    const double t = 2.0 - R, s = fmax(1.0 - R, 0.0);
+    return __fma_rn(-4.0 * s, s * s, t * t * t);
+}
+
+// r = sqrt(r^2) for the density (the neighbour decision never uses it).
+__device__ __forceinline__ double dist64(double r2) { return r2 > 0.0 ? r2 * rsqrt(r2) : 0.0; }
+
 enum { P64_COUNT = 0, P64_EMIT = 1 };
 
 // One pass of kept candidates: windows staged, tested (bits of kept slot k
@@ -171,7 +183,7 @@ __device__ __forceinline__ void run_pass64(Smem64 &S, const GridDev &g, const do
                         ++cnt;
                     } else {
                         ++cnt;
-                        if (dens) acc += w_poly64(__dsqrt_rn(r2_staged<DIM>(S, xi, c)) * g.r_scale64);
+                        if (dens) acc += six_p64(dist64(r2_staged<DIM>(S, xi, c)) * g.r_scale64);
                     }
                 }
             }
@@ -244,7 +256,7 @@ __global__ void __launch_bounds__(32 * WPB64, CTA_PER_SM64)
         if (col != nullptr && !wc && lane == 0) atomicOr(&g.status->flags, ST_CAPACITY);
         if (mine) {
             row_ptr[i] = pre + rstart;
-            if (dens) rho[i] = (float)(g.w_self64 + g.w_norm64 * acc);
+            if (dens) rho[i] = (float)(g.w_self64 + g.w_norm64 * (acc * (1.0 / 6.0)));
         }
         if (t == ntiles - 1 && lane == 0) row_ptr[g.n] = pre + agg;
         if (!wc) continue;

@@ -244,6 +244,30 @@ __global__ void __launch_bounds__(SORT_NT) k_seg_sort_small(int *keys, const Idx
             int v = lane < len ? keys[a + lane] : 0;
             v = warp_sort32(v, lane, (int)len);
             if (lane < len) keys[a + lane] = v;
+        } else if (len <= 64) {
+            int v[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) v[t] = t * 32 + lane < len ? keys[a + t * 32 + lane] : 0x7fffffff;
+            warp_sort_reg<2>(v, lane);
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                if (t * 32 + lane < len) keys[a + t * 32 + lane] = v[t];
+        } else if (len <= 128) {
+            int v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] = t * 32 + lane < len ? keys[a + t * 32 + lane] : 0x7fffffff;
+            warp_sort_reg<4>(v, lane);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (t * 32 + lane < len) keys[a + t * 32 + lane] = v[t];
+        } else if (len <= 256) {
+            int v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = t * 32 + lane < len ? keys[a + t * 32 + lane] : 0x7fffffff;
+            warp_sort_reg<8>(v, lane);
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (t * 32 + lane < len) keys[a + t * 32 + lane] = v[t];
         } else if (len <= WARP_SMEM_KEYS) {
             int *buf = wbuf[w];
             for (int i = lane; i < len; i += 32) buf[i] = keys[a + i];

@@ -108,7 +108,9 @@ void free_result(sph_server_s *S, Req *q) {
 
 struct ServerWorker {
     sph_server_s *S;
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr;     // stream of the current request
+    cudaStream_t s_hi = nullptr;  // high priority: requests of up to large_n particles, batches
+    cudaStream_t s_lo = nullptr;  // low priority: larger requests
     sph_grid_t grid = nullptr;
     sph_batch_t batch = nullptr;
     DevBuf xyz, brp, bcol, brho, borig;
@@ -118,12 +120,15 @@ struct ServerWorker {
         const sph_request &r = q->r;
         const int dim = r.params.dim;
         const double *x = r.xyz;
+        const bool large = r.n > S->sc.large_n;
+        s = large ? s_lo : s_hi;
         if (r.n > 0 && !r.xyz_on_device) {
             SPH_TRY(ensure(xyz, (size_t)r.n * dim * sizeof(double), s));
             SPH_CUDA(cudaMemcpyAsync(xyz.p, r.xyz, (size_t)r.n * dim * sizeof(double), cudaMemcpyHostToDevice, s));
             x = P<double>(xyz);
         }
         SPH_TRY(sph_bin_cells(&r.params, x, r.n, s, &grid));
+        SPH_TRY(sph_grid_set_option(grid, SPH_OPT_SM_SHARE, large ? S->sc.large_sm_percent : 100));
         SPH_TRY(ensure(q->rp, (size_t)(r.n + 1) * sizeof(int64_t), s));
         if (r.want_density) SPH_TRY(ensure(q->rho, (size_t)(r.n > 0 ? r.n : 1) * sizeof(float), s));
         // the search writes straight into the request's column buffer, sized
@@ -155,6 +160,7 @@ struct ServerWorker {
 
     // Several small cell-order requests of one dimension as one batched run.
     int run_batch(std::vector<Req *> &qs) {
+        s = s_hi;
         const int k = (int)qs.size();
         const int dim = qs[0]->r.params.dim;
         int64_t ntot = 0;
@@ -325,28 +331,54 @@ extern "C" int sph_server_create(const sph_server_cfg *cfg, sph_server_t *server
     S->sc.max_batch = cfg->max_batch > 0 ? cfg->max_batch : 64;
     S->sc.batch_max_n = 8 * S->sc.small_n;
     S->sc.max_wait_ns = cfg->max_wait_ns > 0 ? cfg->max_wait_ns : 20000000;
+    S->sc.large_n = cfg->large_n > 0 ? cfg->large_n : 262144;
+    S->sc.large_sm_percent = cfg->large_sm_percent > 0 && cfg->large_sm_percent <= 100 ? cfg->large_sm_percent : 75;
     if (cudaGetDevice(&S->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S->release_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         delete S;
         return fail(SPH_ERR_CUDA, "CUDA initialisation failed");
     }
-    // keep freed result memory in the stream-ordered pool up to the budget
+    // keep freed result memory in the stream-ordered pool up to the budget,
+    // and grow the pool to it now (halving on failure down to 256 MiB): a
+    // request whose allocation has to grow the pool waits for the mapping,
+    // and every worker's allocations wait with it
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
         uint64_t thr = (uint64_t)cfg->hbm_budget_bytes;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        if (cfg->reserve_pool != -1) {
+            size_t free_b = 0, total_b = 0;
+            cudaMemGetInfo(&free_b, &total_b);
+            size_t want = (size_t)cfg->hbm_budget_bytes;
+            if (want > free_b / 10 * 9) want = free_b / 10 * 9;
+            for (; want >= ((size_t)256 << 20); want /= 2) {
+                void *p = nullptr;
+                if (cudaMallocAsync(&p, want, S->release_stream) == cudaSuccess) {
+                    cudaFreeAsync(p, S->release_stream);
+                    cudaStreamSynchronize(S->release_stream);
+                    break;
+                }
+                cudaGetLastError();
+            }
+        }
     }
+    cudaGetLastError();
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     cudaGetLastError();
     const int nw = cfg->streams > 0 ? cfg->streams : 2;
     for (int i = 0; i < nw; ++i) {
         ServerWorker *w = new ServerWorker();
         w->S = S;
-        if (cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&w->s_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&w->s_lo, cudaStreamNonBlocking, prio_lo) != cudaSuccess) {
             cudaGetLastError();
+            if (w->s_hi) cudaStreamDestroy(w->s_hi);
             delete w;
             break;
         }
+        w->s = w->s_hi;
         // batches of waiting requests change shape every time: no graph
         // recording, staging sized from the density estimate (no timing runs)
         if (sph_batch_create(&w->batch) == SPH_OK) {
@@ -509,13 +541,15 @@ extern "C" int sph_server_destroy(sph_server_t S) {
     S->cv_work.notify_all();
     for (auto &t : S->threads) t.join();
     for (ServerWorker *w : S->workers) {
-        cudaStreamSynchronize(w->s);
+        cudaStreamSynchronize(w->s_hi);
+        cudaStreamSynchronize(w->s_lo);
         if (w->grid) sph_grid_free(w->grid);
         if (w->batch) sph_batch_free(w->batch);
         DevBuf *bufs[] = {&w->xyz, &w->brp, &w->bcol, &w->brho, &w->borig};
         for (DevBuf *b : bufs) release(*b, w->s);
         cudaStreamSynchronize(w->s);
-        cudaStreamDestroy(w->s);
+        cudaStreamDestroy(w->s_hi);
+        cudaStreamDestroy(w->s_lo);
         delete w;
     }
     for (auto &kv : S->reqs) {

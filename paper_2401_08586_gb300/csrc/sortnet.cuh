@@ -25,6 +25,32 @@ __device__ __forceinline__ int warp_sort32(int v, int lane, int len) {
     return v;
 }
 
+// One warp sorts keys[0, len) (len <= 32 R) held in registers: v[t] is
+// position t * 32 + lane.  The same bitonic network as warp_sort32 over 32 R
+// positions; a comparator's partner is position p ^ m, i.e. register t ^ (m >>
+// 5) of lane lane ^ (m & 31) (a shuffle when m & 31 != 0, else a register of
+// the same lane).  Positions past len hold +infinity.
+template <int R>
+__device__ __forceinline__ void warp_sort_reg(int (&v)[R], int lane) {
+    static_assert(R == 2 || R == 4 || R == 8, "32, 64, 128 or 256 keys");
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int m = (j == (k >> 1)) ? (k - 1) : j;
+            const int ml = m & 31, mt = m >> 5;
+            int o[R];
+#pragma unroll
+            for (int t = 0; t < R; ++t) o[t] = ml ? __shfl_xor_sync(0xffffffffu, v[t ^ mt], ml) : v[t ^ mt];
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int p = t * 32 + lane, q = p ^ m;
+                v[t] = p < q ? min(v[t], o[t]) : max(v[t], o[t]);
+            }
+        }
+    }
+}
+
 // Compare-exchange network over keys[0, len) in any memory, executed by
 // `nthr` cooperating threads with index `t`; `sync` orders the steps.
 template <typename Sync>

@@ -70,7 +70,8 @@ class sph_batch_stats(ctypes.Structure):
 
 class sph_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("small_n", ctypes.c_int64), ("max_wait_ns", ctypes.c_int64)]
+                ("small_n", ctypes.c_int64), ("max_wait_ns", ctypes.c_int64), ("large_n", ctypes.c_int64),
+                ("large_sm_percent", ctypes.c_int32), ("reserve_pool", ctypes.c_int32)]
 
 
 class sph_request(ctypes.Structure):
@@ -194,6 +195,7 @@ SPH_OPT_FUSED = 1
 SPH_OPT_STAGING = 2
 SPH_OPT_TILE_SHAPE = 3
 SPH_OPT_TEST_LOOKBACK = 4
+SPH_OPT_SM_SHARE = 5
 
 
 def sph_grid_set_option(grid, option, value):
@@ -529,9 +531,11 @@ class Server:
     """Request server (see include/sph.h).  ``submit`` keeps a reference to
     the coordinates until the request is released."""
 
-    def __init__(self, budget_bytes, streams=0, max_batch=0, small_n=0, max_wait_ns=0):
+    def __init__(self, budget_bytes, streams=0, max_batch=0, small_n=0, max_wait_ns=0, large_n=0,
+                 large_sm_percent=0, reserve_pool=0):
         self.handle = None
-        self.handle = sph_server_create(sph_server_cfg(int(budget_bytes), streams, max_batch, small_n, max_wait_ns))
+        self.handle = sph_server_create(sph_server_cfg(int(budget_bytes), streams, max_batch, small_n, max_wait_ns,
+                                                       large_n, large_sm_percent, reserve_pool))
         self._keep = {}
 
     def submit(self, xyz, params, density=True):

@@ -344,3 +344,18 @@ def test_density_half_stencil(sph, case):
     r[out["orig"]] = half
     assert (np.abs(r - rho_ref) / rho_ref).max() <= RHO_RTOL
     assert (np.abs(half - out["rho"]) / out["rho"]).max() <= 2e-6
+
+
+@pytest.mark.parametrize("dim,khr", [(2, 2.4), (2, 4.0), (3, 2.6), (3, 3.6), (3, 4.6)])
+def test_canonical_row_lengths(sph, dim, khr):
+    """Canonical order sorts each row's input-order columns: rows of about
+    20, 50, 80, 190 and 400 neighbours exercise the one-register, 64-, 128-
+    and 256-key register networks and the shared-memory network."""
+    side = 60 if dim == 2 else 16
+    dx = 1.0 / side
+    xyz = W.lattice((side,) * dim, dx, 0.1, seed=31 + int(10 * khr))
+    h = 0.5 * khr * dx
+    out = run(sph, xyz, h, 2 * h, 1)
+    check_against_oracle(out, xyz, h, 2 * h, 1)
+    lens = np.diff(out["rp"])
+    assert lens.max() > {2.4: 16, 4.0: 40, 2.6: 64, 3.6: 128, 4.6: 256}[khr]

@@ -182,3 +182,56 @@ def test_tickets_and_shutdown(sph):
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 60
+
+
+def _fetch_host(srv, t):
+    rp, col, rho, orig = srv.fetch(t)
+    return (rp.cpu().numpy(), col.cpu().numpy(), rho.cpu().numpy(),
+            None if orig is None else orig.cpu().numpy())
+
+
+def test_same_result_alone_and_in_the_mix(sph):
+    """Each request's result is the same when it is served alone and when it
+    is served inside a mixed load: small requests of both dimensions batched
+    together (continuous batching, results split by the rebase kernels), a
+    large request on its low-priority stream with a share of the GPU, and
+    canonical-order requests, all submitted at once to four workers.  CSR
+    identical; density within 1e-5 relative (the batched search may pick
+    another tile shape, whose summation order differs in the last bits); the
+    cell-order permutation identical."""
+    specs = [(300000, 3, 0), (4000, 3, 0), (2500, 3, 0), (9000, 3, 0), (1500, 2, 0), (6000, 2, 0),
+             (20000, 3, 1), (3000, 2, 1), (700, 3, 0), (12000, 3, 0), (60000, 2, 0), (5000, 3, 0)]
+    systems = []
+    for k, (n, dim, order) in enumerate(specs):
+        xyz, h = lattice_system(n, dim, 100 + k, hr=1.2 + 0.025 * k)
+        systems.append((torch.from_numpy(xyz).cuda(), sph.make_params(dim, h, 2 * h, order=order)))
+
+    # alone: one worker, one request at a time, no batching partner
+    srv = sph.Server(16 * GB, streams=1)
+    alone = []
+    for x, p in systems:
+        t = srv.submit(x, p)
+        assert srv.wait(t).status == sph.SPH_OK
+        alone.append(_fetch_host(srv, t))
+        srv.release(t)
+    assert srv.stats().batches == 0
+    srv.close()
+
+    # in the mix: everything at once
+    srv = sph.Server(16 * GB, streams=4, large_n=100000, large_sm_percent=60)
+    ts = [srv.submit(x, p) for x, p in systems]
+    mixed = []
+    for t in ts:
+        assert srv.wait(t).status == sph.SPH_OK
+        mixed.append(_fetch_host(srv, t))
+    st = srv.stats()
+    srv.close()
+    assert st.batches >= 1 and st.batched_requests >= 2
+
+    for k, (a, b) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(a[0], b[0]), ("row_ptr", k)
+        assert np.array_equal(a[1], b[1]), ("col", k)
+        if a[3] is not None or b[3] is not None:
+            assert np.array_equal(a[3], b[3]), ("orig_id", k)
+        rel = np.abs(a[2].astype(np.float64) - b[2]) / np.abs(a[2].astype(np.float64))
+        assert rel.max() <= RHO_RTOL, (k, rel.max())
