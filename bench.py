@@ -202,13 +202,21 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "n_particles": ps.n},
+        "config": workload_config(desc, ps, world),
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": threads, "kind": "oracle",
                          "sample": "full workload per step (FP64 cell link-list + density, OpenMP rows)"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_config(desc, ps, world):
+    """The bench line's `config`, the same for both arms (the workload, its
+    size and the output form; L2 handling of the GPU arm's timing)."""
+    return {"workload": desc, "n_particles": ps.n, "dim": ps.dim, "order": "cell",
+            "density": "fused, fp32 accumulation", "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def run_reference_systems(args, threads):
@@ -412,9 +420,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms_mean, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": desc, "n_particles": n, "dim": ps.dim, "order": "cell",
-                   "density": "fused, fp32 accumulation", "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(desc, ps, world),
         "clocks": clocks,
         "gpu_launches": launches,
         "roofline": roofline,
@@ -432,6 +438,8 @@ def main():
                                       line.get("roofline", {}).get("launch_ms"))
         line["fp64_cll"]["device_fp64_fma_tflops"] = sph.sph_device_fp64_rate() / 1e12
         line["query_variants"] = bench_query_variants(sph, ps, xyz, dev, stream, max(3, min(args.steps, 20)))
+        if args.workload == "3d_1m" and SIDE == 100:
+            line["c3_8m"] = bench_c3(sph, dev, stream, max(3, min(args.steps, 10)), peak, peak_src)
         line["e2e"] = bench_e2e(sph, ps, dev, stream, args)
         if world > 1:
             line["e2e"]["value"] = world * n * args.steps / replicas.max_over_ranks(line["e2e"]["seconds"], world,
@@ -504,6 +512,60 @@ def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value, fp16_search_ms=None
     if fp16_search_ms and search_ms:
         out["search_speedup"] = search_ms / fp16_search_ms
     return out
+
+
+def bench_c3(sph, dev, stream, steps, peak, peak_src):
+    """The 8M non-uniform dam-break set (C3): the same step (binning + tile
+    search with fused density, cell order), CUDA events per step, the search
+    launch timed by the library's events and its HBM roofline (36 B per
+    particle + 4 B per neighbour)."""
+    import torch
+    from paper_2401_08586_gb300 import workloads as W
+    ps = W.c3_3d_dambreak()
+    n = ps.n
+    sptr = stream.cuda_stream
+    xyz = torch.from_numpy(ps.xyz).to(dev)
+    params = sph.make_params(ps.dim, ps.h, ps.kh, order=sph.SPH_ORDER_CELL)
+    g = sph.sph_bin_cells(params, xyz, n, sptr, None)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    nnz = sph.sph_nnps_query(g, rp, None, 0, True, None, sptr)
+    col = torch.empty(nnz + 1024, dtype=torch.int32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sph.sph_bin_cells(params, xyz, n, sptr, g)
+        sph.sph_nnps_query(g, rp, col, col.numel(), False, rho, sptr)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    sph.sph_profile_reset()
+    sph.sph_profile_select("fused")
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    sph.sph_profile_enable(False)
+    fms, fc = sph.sph_profile_read("fused")
+    sph.sph_grid_check(g, sptr)
+    sph.sph_grid_free(g)
+    t = sum(ms) / steps
+    launch = fms / fc
+    alg = n * (8 + 16 + 8 + 4) + 4 * nnz
+    achieved = alg / (launch * 1e-3) / 1e9
+    return {"workload": "3d_8m_dambreak: 200^3 lattice dx=1/200 in z<1 of a 1x1x2 box, 5% spray in z in (1,2], "
+                        "jitter U(+-0.2dx), h=1.5dx, kh=3dx, seed 3",
+            "n_particles": n, "value": n / (t * 1e-3), "unit": "particles/s", "ms_per_step": t, "steps": steps,
+            "nnz": nnz, "neighbours_per_particle": nnz / n,
+            "roofline": {"bound": "hbm", "kernel": "k_nnps_tile", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "launch_ms": launch,
+                         "algorithmic_bytes_per_launch": alg}}
 
 
 def bench_query_variants(sph, ps, xyz, dev, stream, steps):
@@ -670,9 +732,23 @@ def bench_e2e(sph, ps, dev, stream, args):
         t0 = time.perf_counter()
         sph.sph_search_host(params, xyz_h, n, rho_h, sptr, g)
         t += time.perf_counter() - t0
+    # the same with the whole CSR copied back to pinned host memory as well
+    rp_h = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    col_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+    steps_csr = max(3, args.steps // 4)
+    t_csr = 0.0
+    for k in range(steps_csr):
+        t0 = time.perf_counter()
+        _, nnz_k = sph.sph_search_host(params, xyz_h, n, rho_h, sptr, g)
+        sph.sph_grid_csr_copy(g, rp_h, col_h, sptr)
+        t_csr += time.perf_counter() - t0
     sph.sph_grid_free(g)
     return {"value": n * args.steps / t, "unit": "particles/s", "h2d_bytes_per_step": n * ps.dim * 8,
-            "d2h_bytes_per_step": n * 4 + 8, "seconds": t}
+            "d2h_bytes_per_step": n * 4 + 8, "seconds": t,
+            "with_csr": {"value": n * steps_csr / t_csr, "unit": "particles/s", "steps": steps_csr,
+                         "h2d_bytes_per_step": n * ps.dim * 8,
+                         "d2h_bytes_per_step": n * 4 + 8 + (n + 1) * 8 + nnz * 4,
+                         "note": "sph_search_host, then sph_grid_csr_copy of row_ptr and col to pinned host memory"}}
 
 
 SERVE_DESC = ("serve: Poisson arrivals at 200 req/s, 70%% 3D / 30%% 2D, N log-uniform in [1e3, 2e6], jittered "
@@ -821,8 +897,19 @@ def bench_batch(args, sph, dev, world, rank, local):
         t1 = time.perf_counter()
     launches = sph.sph_launch_count() - launches0
     sph.sph_profile_enable(False)
-    ms, c = sph.sph_profile_read("fused")
     st = b.stats()
+    # the search runs inside the replayed graph, where no per-launch events are
+    # recorded: its launch time comes from an untimed pass of direct launches
+    b.set_option(sph.SPH_BATCH_OPT_GRAPH, 0)
+    sph.sph_profile_reset()
+    sph.sph_profile_select("fused")
+    for k in range(3):
+        flush.fill_(float(k))
+        b.run(pairs, stream=stream)
+    torch.cuda.synchronize()
+    sph.sph_profile_enable(False)
+    ms, c = sph.sph_profile_read("fused")
+    b.set_option(sph.SPH_BATCH_OPT_GRAPH, 1)
     total_s = sum(a.elapsed_time(e) for a, e in evs) / 1e3
     nnz = int(rp[-1].item())
     value = replicas.whole_job_rate(ntot * args.steps, total_s, world, dev)
@@ -844,6 +931,8 @@ def bench_batch(args, sph, dev, world, rank, local):
                      "algorithmic_bytes_per_launch": alg, "traffic": None},
         "nnz": nnz, "neighbours_per_particle": nnz / ntot, "wall_s_timed": t1 - t0,
         "batch": {"graph_replays_timed": st.graph_replays - st0.graph_replays, "graph_captures": st.graph_captures,
+                  "graph_holds": "binning, tile list, counter reset and the persistent tile search",
+                  "direct_launches_last_run": st.direct_launches,
                   "tuned_staging_bytes": st.tuned_staging, "fp32_pairs": st.fp32_pairs, "fp64_pairs": st.fp64_pairs},
     }
     if not args.no_extras:

@@ -343,6 +343,11 @@ int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, floa
 
 /* Device pointers of the grid-owned CSR and density written by the last
  * sph_search_host on this grid (host out-pointers; any may be NULL). */
+/* Copy the CSR written by the last sph_search_host on this grid into caller
+ * buffers (host -- preferably pinned -- or device; any may be NULL): row_ptr
+ * int64[n + 1], col int32[nnz], on `stream`, then synchronise it.
+ * SPH_ERR_INVALID when the grid holds no sph_search_host result. */
+int sph_grid_csr_copy(sph_grid_t grid, int64_t *row_ptr, int32_t *col, void *stream);
 int sph_grid_csr(sph_grid_t grid, const int64_t **row_ptr, const int32_t **col, const float **rho,
                  int64_t *nnz);
 
@@ -422,13 +427,17 @@ typedef struct {
     int32_t reserved;
     int64_t fp32_pairs;       /* last run: pairs re-decided in FP32 */
     int64_t fp64_pairs;       /* last run: pairs decided in FP64 */
+    int64_t direct_launches;  /* last run: kernels launched outside the replayed graph */
+    int64_t graph_launched;   /* last run: 1 if it launched the recorded graph, else 0 */
 } sph_batch_stats;
 int sph_batch_get_stats(sph_batch_t batch, sph_batch_stats *stats);
 
-/* SPH_BATCH_OPT_GRAPH: 1 (default) record the binning and tile-list launches
- *   (after the bounds, before the search) as a CUDA graph and replay it while
- *   the batch's sizes and buffers are unchanged; 0 launch directly every time.
- *   The search is one direct launch either way.
+/* SPH_BATCH_OPT_GRAPH: 1 (default) record the launches after the bounds --
+ *   binning, tile list, counter reset and the persistent tile search with the
+ *   shape and staging chosen for the batch -- as one CUDA graph and replay it
+ *   while the batch's sizes, buffers and chosen shape are unchanged (a run
+ *   that tunes the shape runs directly and records the graph with its
+ *   choice); 0 launch directly every time.
  * SPH_BATCH_OPT_STAGING: -1 (default) tune the tile search's shape and
  *   staging bytes by timing five candidates (sparse 0 / 2048, dense 0 / 2048 /
  *   4096) on the first run of each density class (dimension and neighbours per

@@ -79,10 +79,11 @@ static GridDev make_dev(sph_grid_s *g) {
     return d;
 }
 
-// Copy the status record to the host mirror and wait.
-static int read_status(sph_grid_s *g) {
-    SPH_CUDA(cudaMemcpyAsync(g->h_status, g->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost,
-                             g->stream));
+// Copy the status record (and, if rp_nnz != NULL, the nnz at rp_nnz) to
+// the pinned host mirror and wait.  A kernel writes the mirror: no copy
+// engine on the control path.
+static int read_status(sph_grid_s *g, const long long *rp_nnz = nullptr) {
+    SPH_CUDA(status_to_host(g->h_status, P<DevStatus>(g->status), rp_nnz, g->stream));
     SPH_CUDA(cudaStreamSynchronize(g->stream));
     return SPH_OK;
 }
@@ -316,8 +317,7 @@ static int run_tile_search(sph_grid_s *g, long long *rp_cell, int *col, long lon
 
 // nnz of a finished cell-order search (rp_cell[n]); synchronises the stream.
 static int read_nnz(sph_grid_s *g, const long long *rp_cell, long long *nnz) {
-    SPH_CUDA(cudaMemcpyAsync(&g->h_status->nnz, rp_cell + g->n, sizeof(long long), cudaMemcpyDeviceToHost, g->stream));
-    SPH_CUDA(cudaStreamSynchronize(g->stream));
+    SPH_TRY(read_status(g, rp_cell + g->n));
     *nnz = g->h_status->nnz;
     if (g->n > 0) g->last_nbr = (double)*nnz / (double)g->n;
     return SPH_OK;
@@ -373,8 +373,7 @@ extern "C" int sph_nnps_query(sph_grid_t grid, int64_t *row_ptr, int32_t *col, i
         }
         if (nnz_out) {
             long long nnz_host = 0;
-            SPH_TRY(read_nnz(g, rp_cell, &nnz_host));
-            SPH_TRY(read_status(g));
+            SPH_TRY(read_nnz(g, rp_cell, &nnz_host));  // the status record comes with it
             *nnz_out = nnz_host;
             int rc = status_to_code(g->h_status->flags);
             if (rc == SPH_OK && col && nnz_host > col_capacity)
@@ -546,9 +545,9 @@ extern "C" int sph_grid_export(sph_grid_t grid, int32_t *orig_id, int32_t *rank,
     if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (orig_id && g->n)
-        SPH_CUDA(cudaMemcpyAsync(orig_id, g->orig_id.p, g->n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(copy_d2d_kernel(orig_id, g->orig_id.p, g->n * sizeof(int), s));
     if (rank && g->n)
-        SPH_CUDA(cudaMemcpyAsync(rank, g->rank.p, g->n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(copy_d2d_kernel(rank, g->rank.p, g->n * sizeof(int), s));
     if (cell_start && g->cell_start.p)
         SPH_CUDA(cudaMemcpyAsync(cell_start, g->cell_start.p, (g->ncell + 1) * sizeof(int),
                                  cudaMemcpyDeviceToDevice, s));
@@ -638,6 +637,19 @@ extern "C" int sph_search_host(const sph_params *p, const double *xyz_host, int6
         SPH_CUDA(cudaMemcpyAsync(rho_host, g->own_rho.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
     SPH_CUDA(cudaStreamSynchronize(s));
     if (nnz_host) *nnz_host = nnz;
+    return SPH_OK;
+}
+
+extern "C" int sph_grid_csr_copy(sph_grid_t grid, int64_t *row_ptr, int32_t *col, void *stream) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (!g->own_rp.p) return fail(SPH_ERR_INVALID, "the grid holds no sph_search_host result");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (row_ptr)
+        SPH_CUDA(cudaMemcpyAsync(row_ptr, g->own_rp.p, (size_t)(g->n + 1) * sizeof(int64_t), cudaMemcpyDefault, s));
+    if (col && g->own_nnz > 0)
+        SPH_CUDA(cudaMemcpyAsync(col, g->own_col.p, (size_t)g->own_nnz * sizeof(int32_t), cudaMemcpyDefault, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
     return SPH_OK;
 }
 

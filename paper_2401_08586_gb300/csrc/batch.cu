@@ -12,11 +12,12 @@
 // CSR over the concatenation.
 //
 // After the bounds (one device->host read for all systems), the launches of
-// the binning and tile-list steps depend only on the batch's shapes and
-// buffers: they are recorded once as a CUDA graph and replayed while those
-// stay the same.  The tile search itself is one persistent launch after the
-// graph; its staging size is tuned by timing the candidates on the first run
-// of each density class.
+// the binning, tile-list and search steps depend only on the batch's shapes,
+// buffers and the chosen tile shape: they are recorded once as a CUDA graph
+// (the persistent search included) and replayed while those stay the same.
+// The tile shape and staging are tuned by timing the candidates on the first
+// run of each density class; that run launches directly and records the
+// graph with its choice.
 #include <math.h>
 #include <string.h>
 
@@ -206,6 +207,7 @@ unsigned grid_blocks(long long n, int nt, int sm_count, int per_sm) {
 struct GraphKey {
     long long ntot, ncell, nrow, ntiles_max, cap;
     int nsys, dim;
+    int shape, extra;  // the search's tile shape and staging
     const void *ptrs[32];
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
@@ -393,6 +395,7 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     cudaStream_t s = (cudaStream_t)stream;
     SPH_TRY(batch_host_tables(b, nsys));
 
+    const long long launches_before = launch_count();
     // ---- per-system bounds (one read for all systems) -------------------------
     long long nn = ntot > 0 ? ntot : 1;
     SPH_TRY(ensure(b->status, sizeof(DevStatus), s));
@@ -431,8 +434,8 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
                                                                               P<DevStatus>(b->status));
         }
         SPH_CUDA(cudaGetLastError());
-        SPH_CUDA(cudaMemcpyAsync(b->h_keys, b->keys.p, (size_t)nsys * 6 * 8, cudaMemcpyDeviceToHost, s));
-        SPH_CUDA(cudaMemcpyAsync(b->h_status, b->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        SPH_CUDA(copy_small_to_host(b->h_keys, b->keys.p, (size_t)nsys * 6 * 8, s));
+        SPH_CUDA(status_to_host(b->h_status, P<DevStatus>(b->status), nullptr, s));
         SPH_CUDA(cudaStreamSynchronize(s));
         if (b->h_status->flags & ST_NONFINITE) return fail(SPH_ERR_INVALID, "non-finite particle coordinate");
     }
@@ -555,51 +558,26 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
     static_assert(sizeof(ptrs) / sizeof(ptrs[0]) <= sizeof(key.ptrs) / sizeof(key.ptrs[0]), "GraphKey slots");
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) key.ptrs[k] = ptrs[k];
 
+    key.shape = tv.shape;
+    key.extra = tv.extra;
+
     b->stats.runs++;
+    b->stats.graph_launched = 0;
+    long long graph_kernels = 0;  // kernels of a replayed graph (counted as launches too)
     if (ntot == 0) {
         SPH_CUDA(cudaMemsetAsync(out->row_ptr, 0, sizeof(int64_t), s));
+    } else if (!tune && b->use_graph && b->exec && b->key == key) {
+        // binning, tile list and search: one graph launch
+        SPH_CUDA(cudaGraphLaunch(b->exec, s));
+        note_launch((int)b->graph_launches);
+        graph_kernels = b->graph_launches;
+        b->stats.graph_replays++;
+        b->stats.graph_launched = 1;
     } else {
-        // binning and tile list: the replayed graph, or direct launches
-        // (recorded for the next run unless the graph is switched off)
-        if (b->use_graph && b->exec && b->key == key) {
-            SPH_CUDA(cudaGraphLaunch(b->exec, s));
-            note_launch((int)b->graph_launches);
-            b->stats.graph_replays++;
-        } else {
-            cudaError_t e = batch_prep(b, nsys, dim, ntot, ncell, nrow, out, s);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(SPH_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
-            }
-            if (b->use_graph) {
-                if (b->exec) {
-                    cudaGraphExecDestroy(b->exec);
-                    b->exec = nullptr;
-                }
-                cudaGraph_t graph = nullptr;
-                const long long l0 = launch_count();
-                prof_set_capturing(true);
-                cudaError_t ce = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
-                if (ce == cudaSuccess) {
-                    ce = batch_prep(b, nsys, dim, ntot, ncell, nrow, out, b->cap_stream);
-                    cudaError_t ce2 = cudaStreamEndCapture(b->cap_stream, &graph);
-                    if (ce == cudaSuccess) ce = ce2;
-                }
-                prof_set_capturing(false);
-                // captured work does not run: take the recorded launches back
-                // out of the launch count; each replay adds them
-                b->graph_launches = launch_count() - l0;
-                note_launch(-(int)b->graph_launches);
-                if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
-                if (ce != cudaSuccess) {
-                    cudaGetLastError();
-                    b->exec = nullptr;
-                } else {
-                    b->key = key;
-                    b->stats.graph_captures++;
-                }
-            }
+        cudaError_t e = batch_prep(b, nsys, dim, ntot, ncell, nrow, out, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPH_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
         }
         // the search: tuned candidates are timed here (each run leaves the
         // same result), then one launch with the chosen staging
@@ -620,16 +598,51 @@ extern "C" int sph_batch_run(sph_batch_t *batch, const sph_params *per_system, c
             b->stats.tuned_shape = best.shape;
             b->stats.tuned_candidates = (int)(sizeof(cand) / sizeof(cand[0]));
             tv = best;
+            key.shape = tv.shape;
+            key.extra = tv.extra;
         }
         SPH_CUDA(launch_status_reset_counters(P<DevStatus>(b->status), s));
         SPH_CUDA(batch_search(b, dim, ntot, nrow, ntiles_max, out, tv, s));
+        // record the whole sequence for the next run with these shapes
+        if (b->use_graph) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            const long long l0 = launch_count();
+            prof_set_capturing(true);
+            cudaError_t ce = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
+            if (ce == cudaSuccess) {
+                ce = batch_prep(b, nsys, dim, ntot, ncell, nrow, out, b->cap_stream);
+                if (ce == cudaSuccess) ce = launch_status_reset_counters(P<DevStatus>(b->status), b->cap_stream);
+                if (ce == cudaSuccess) ce = batch_search(b, dim, ntot, nrow, ntiles_max, out, tv, b->cap_stream);
+                cudaError_t ce2 = cudaStreamEndCapture(b->cap_stream, &graph);
+                if (ce == cudaSuccess) ce = ce2;
+            }
+            prof_set_capturing(false);
+            // captured work does not run: take the recorded launches back out
+            // of the launch count; each replay adds them
+            b->graph_launches = launch_count() - l0;
+            note_launch(-(int)b->graph_launches);
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                b->exec = nullptr;
+            } else {
+                b->key = key;
+                b->stats.graph_captures++;
+            }
+        }
     }
+    b->stats.direct_launches = launch_count() - launches_before - graph_kernels;
 
     // ---- nnz, status ------------------------------------------------------------
-    SPH_CUDA(cudaMemcpyAsync(b->h_nnz, out->row_ptr + ntot, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaMemcpyAsync(b->h_status, b->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(status_to_host(b->h_status, P<DevStatus>(b->status), reinterpret_cast<const long long *>(out->row_ptr) + ntot,
+                            s));
     SPH_CUDA(cudaStreamSynchronize(s));
-    out->nnz = *b->h_nnz;
+    out->nnz = b->h_status->nnz;
     b->stats.fp32_pairs = (int64_t)b->h_status->fp32_pairs;
     b->stats.fp64_pairs = (int64_t)b->h_status->fp64_pairs;
     int rc = status_to_code(b->h_status->flags & ~(unsigned)ST_CAPACITY);

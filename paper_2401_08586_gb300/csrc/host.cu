@@ -157,6 +157,57 @@ __global__ void k_status_reset_counters(DevStatus *st, unsigned long long first_
     st->flags &= ~(ST_CAPACITY | ST_TIMEOUT);
 }
 
+__global__ void k_copy_words(unsigned int *__restrict__ dst, const unsigned int *__restrict__ src, long long words) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+__global__ void k_status_to_host(DevStatus *host, const DevStatus *st, const long long *nnz_src) {
+    const unsigned int *src = reinterpret_cast<const unsigned int *>(st);
+    unsigned int *dst = reinterpret_cast<unsigned int *>(host);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevStatus) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0 && nnz_src != nullptr) host->nnz = *nnz_src;
+}
+
+__global__ void k_gather_i64(long long *host, const long long *src, const long long *idx, int count) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) host[i] = src[idx[i]];
+}
+
+cudaError_t copy_small_to_host(void *host_dst, const void *dev_src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    note_launch(1);
+    k_copy_words<<<1, 128, 0, s>>>(static_cast<unsigned int *>(host_dst), static_cast<const unsigned int *>(dev_src),
+                                   (long long)(bytes / 4));
+    return cudaGetLastError();
+}
+
+cudaError_t status_to_host(DevStatus *host_dst, const DevStatus *dev_src, const long long *nnz_src, cudaStream_t s) {
+    static_assert(sizeof(DevStatus) % 4 == 0, "status record in words");
+    note_launch(1);
+    k_status_to_host<<<1, 32, 0, s>>>(host_dst, dev_src, nnz_src);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_i64_to_host(long long *host_dst, const long long *src, const long long *idx, int count,
+                               cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    note_launch(1);
+    k_gather_i64<<<1, 128, 0, s>>>(host_dst, src, idx, count);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_d2d_kernel(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    const long long words = (long long)(bytes / 4);
+    if (words == 0) return cudaSuccess;
+    long long blocks = (words + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    note_launch(1);
+    k_copy_words<<<(unsigned)blocks, 256, 0, s>>>(static_cast<unsigned int *>(dst), static_cast<const unsigned int *>(src),
+                                                  words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_status_init(DevStatus *st, cudaStream_t s) {
     note_launch(1);
     k_status_init<<<1, 1, 0, s>>>(st);

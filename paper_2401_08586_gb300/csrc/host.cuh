@@ -52,6 +52,25 @@ void set_constants(GridDev &d, const sph_params &p, double hc);
 // The launch-invariant divisors of the grid's cell ids (nk filled first).
 void set_divisors(GridDev &d);
 
+// Small device -> host and device -> device copies done by a kernel instead
+// of a copy engine.  The control path of a query (status record, nnz, a
+// batch's row offsets) and the server's per-request copies then never wait
+// in a copy engine's queue behind another stream's large transfer (a client
+// copying a 600 MB result back).  host_dst: pinned host memory (mapped into
+// the device's address space, as all pinned memory is under unified
+// addressing); bytes and both addresses multiples of 4.  The data is visible
+// to the host once the stream has been synchronised.
+cudaError_t copy_small_to_host(void *host_dst, const void *dev_src, size_t bytes, cudaStream_t s);
+// The status record and, if nnz_src != NULL, the value at nnz_src into the
+// record's nnz field, in one launch.
+cudaError_t status_to_host(DevStatus *host_dst, const DevStatus *dev_src, const long long *nnz_src, cudaStream_t s);
+// host_dst[i] = src[idx[i]] for i < count (int64 gathers into pinned memory;
+// idx in pinned host memory too).
+cudaError_t gather_i64_to_host(long long *host_dst, const long long *src, const long long *idx, int count,
+                               cudaStream_t s);
+// dst[0, bytes) = src[0, bytes) on the device (4-byte multiples).
+cudaError_t copy_d2d_kernel(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
 // Host launchers of the status-record kernels.
 cudaError_t launch_status_init(DevStatus *st, cudaStream_t s);
 cudaError_t launch_status_reset_counters(DevStatus *st, cudaStream_t s, unsigned long long first_ticket = 0);

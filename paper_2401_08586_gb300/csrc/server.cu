@@ -111,6 +111,8 @@ struct ServerWorker {
     cudaStream_t s = nullptr;     // stream of the current request
     cudaStream_t s_hi = nullptr;  // high priority: requests of up to large_n particles, batches
     cudaStream_t s_lo = nullptr;  // low priority: larger requests
+    long long *rp_idx = nullptr, *rp_val = nullptr;  // pinned: a batch's row offsets, read by a kernel
+    int rp_cap = 0;
     sph_grid_t grid = nullptr;
     sph_batch_t batch = nullptr;
     DevBuf xyz, brp, bcol, brho, borig;
@@ -206,15 +208,17 @@ struct ServerWorker {
             if (rc != SPH_ERR_CAPACITY || attempt == 1) return rc;
             cap = out.nnz;
         }
-        // split into per-request buffers
+        // split into per-request buffers: each request's first and last row
+        // offsets, gathered by a kernel into pinned memory
+        if (k + 1 > rp_cap) return fail(SPH_ERR_INVALID, "batch of %d requests exceeds the worker's tables", k);
+        for (int i = 0; i <= k; ++i) rp_idx[i] = first[i];
+        SPH_CUDA(gather_i64_to_host(rp_val, P<long long>(brp), rp_idx, k + 1, s));
+        SPH_CUDA(cudaStreamSynchronize(s));
         std::vector<int64_t> rp_host(2 * k);
         for (int i = 0; i < k; ++i) {
-            SPH_CUDA(cudaMemcpyAsync(&rp_host[2 * i], P<int64_t>(brp) + first[i], sizeof(int64_t),
-                                     cudaMemcpyDeviceToHost, s));
-            SPH_CUDA(cudaMemcpyAsync(&rp_host[2 * i + 1], P<int64_t>(brp) + first[i + 1], sizeof(int64_t),
-                                     cudaMemcpyDeviceToHost, s));
+            rp_host[2 * i] = rp_val[i];
+            rp_host[2 * i + 1] = rp_val[i + 1];
         }
-        SPH_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < k; ++i) {
             Req *q = qs[i];
             const int64_t n = q->r.n, a = first[i], c0 = rp_host[2 * i], c1 = rp_host[2 * i + 1];
@@ -229,11 +233,9 @@ struct ServerWorker {
                 k_rebase_i32<<<blocks_for(q->nnz), 256, 0, s>>>(P<int>(bcol) + c0, P<int>(q->col), q->nnz, (int)a);
             SPH_CUDA(cudaGetLastError());
             if (n > 0) {
-                SPH_CUDA(cudaMemcpyAsync(q->orig.p, P<int32_t>(borig) + a, (size_t)n * sizeof(int32_t),
-                                         cudaMemcpyDeviceToDevice, s));
+                SPH_CUDA(copy_d2d_kernel(q->orig.p, P<int32_t>(borig) + a, (size_t)n * sizeof(int32_t), s));
                 if (q->r.want_density)
-                    SPH_CUDA(cudaMemcpyAsync(q->rho.p, P<float>(brho) + a, (size_t)n * sizeof(float),
-                                             cudaMemcpyDeviceToDevice, s));
+                    SPH_CUDA(copy_d2d_kernel(q->rho.p, P<float>(brho) + a, (size_t)n * sizeof(float), s));
             }
         }
         SPH_CUDA(cudaStreamSynchronize(s));
@@ -379,6 +381,16 @@ extern "C" int sph_server_create(const sph_server_cfg *cfg, sph_server_t *server
             break;
         }
         w->s = w->s_hi;
+        w->rp_cap = S->sc.max_batch + 1;
+        if (cudaMallocHost((void **)&w->rp_idx, (size_t)w->rp_cap * sizeof(long long)) != cudaSuccess ||
+            cudaMallocHost((void **)&w->rp_val, (size_t)w->rp_cap * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            if (w->rp_idx) cudaFreeHost(w->rp_idx);
+            cudaStreamDestroy(w->s_hi);
+            cudaStreamDestroy(w->s_lo);
+            delete w;
+            break;
+        }
         // batches of waiting requests change shape every time: no graph
         // recording, staging sized from the density estimate (no timing runs)
         if (sph_batch_create(&w->batch) == SPH_OK) {
@@ -550,6 +562,8 @@ extern "C" int sph_server_destroy(sph_server_t S) {
         cudaStreamSynchronize(w->s);
         cudaStreamDestroy(w->s_hi);
         cudaStreamDestroy(w->s_lo);
+        cudaFreeHost(w->rp_idx);
+        cudaFreeHost(w->rp_val);
         delete w;
     }
     for (auto &kv : S->reqs) {

@@ -65,7 +65,8 @@ class sph_batch_stats(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int64), ("graph_captures", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("tuned_staging", ctypes.c_int32), ("tuned_candidates", ctypes.c_int32),
                 ("tuned_shape", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("fp32_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64)]
+                ("fp32_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64),
+                ("direct_launches", ctypes.c_int64), ("graph_launched", ctypes.c_int64)]
 
 
 class sph_server_cfg(ctypes.Structure):
@@ -137,6 +138,7 @@ def load(build_if_missing=False):
                             ctypes.POINTER(_vp), _vp],
         "sph_grid_csr": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                          ctypes.POINTER(ctypes.c_int64)],
+        "sph_grid_csr_copy": [_vp, _vp, _vp, _vp],
         "sph_profile_enable": [ctypes.c_int],
         "sph_profile_reset": [],
         "sph_profile_select": [ctypes.c_char_p],
@@ -176,7 +178,7 @@ def exported_symbols():
     """Names of the C-ABI entry points this binding expects."""
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
             "sph_grid_export", "sph_grid_export_rel", "sph_density_half", "sph_grid_check", "sph_grid_free", "sph_last_error",
-            "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr",
+            "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr", "sph_grid_csr_copy",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
             "sph_advance", "sph_gradient_a5", "sph_precision_study", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
@@ -296,6 +298,12 @@ def sph_search_host(params, xyz_host, n, rho_host=None, stream=None, grid=None):
     _check(load().sph_search_host(ctypes.byref(params), _host_ptr(xyz_host), int(n), _host_ptr(rho_host),
                                   ctypes.byref(nnz), ctypes.byref(g), _stream(stream)))
     return g.value, nnz.value
+
+
+def sph_grid_csr_copy(grid, row_ptr=None, col=None, stream=None):
+    """Copy the grid-owned CSR of the last sph_search_host into row_ptr / col
+    (pinned CPU or CUDA tensors, or host numpy arrays); synchronises."""
+    _check(load().sph_grid_csr_copy(grid, _host_ptr(row_ptr), _host_ptr(col), _stream(stream)))
 
 
 def sph_grid_csr(grid):

@@ -134,6 +134,10 @@ def test_graph_replay_and_tuning(sph):
     st = b.stats()
     assert st.graph_replays == 2 and st.graph_captures == captures
     assert sph.sph_launch_count() > launches  # replayed kernels are counted
+    # a replayed run is one graph launch (binning, tile list, counter reset and
+    # the persistent search) plus five small kernels outside it: the status
+    # reset and the bounds before it, the bounds' and the result's read-backs
+    assert st.graph_launched == 1 and st.direct_launches <= 5
     for a, c in zip(r1[:4], r3[:4]):
         assert torch.equal(a, c)
     check_batch(sph, systems, r3)
