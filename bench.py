@@ -447,6 +447,8 @@ def main():
         line["e2e"].pop("seconds", None)
         line["gradient_a5"] = bench_gradient(sph, ps, xyz, grid, row_ptr, col, dev, stream, args.steps)
         line["density_half"] = bench_density_half(sph, ps, grid, dev, stream, args.steps)
+        line["half_stencil_csr"] = bench_half_csr(sph, ps, xyz, dev, stream, max(3, min(args.steps, 10)),
+                                                  line["roofline"]["launch_ms"])
         line["timestep"] = bench_timestep(sph, ps, xyz, dev, stream, row_ptr, col, cap, rho, args.steps)
         line["serving"] = bench_serve(sph, dev, count=2000, warm=200)
         if world == 1 and rank == 0:
@@ -512,6 +514,50 @@ def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value, fp16_search_ms=None
     if fp16_search_ms and search_ms:
         out["search_speedup"] = search_ms / fp16_search_ms
     return out
+
+
+def bench_half_csr(sph, ps, xyz, dev, stream, steps, full_search_ms):
+    """The neighbour list over a half stencil (sph_nnps_query_half: each pair
+    decided once and written into both rows, then a per-row sort) on the
+    step's workload, with the fused density: CUDA events around the call (it
+    reads nnz back to size the fill, so the figure includes that round trip)
+    and the library's kernel times; beside it the tile search's launch."""
+    import torch
+    n = ps.n
+    sptr = stream.cuda_stream
+    params = sph.make_params(ps.dim, ps.h, ps.kh, order=sph.SPH_ORDER_CELL)
+    g = sph.sph_bin_cells(params, xyz, n, sptr, None)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    nnz = sph.sph_nnps_query_half(g, rp, None, 0, None, sptr)
+    col = torch.empty(nnz + 1024, dtype=torch.int32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sph.sph_nnps_query_half(g, rp, col, col.numel(), rho, sptr)
+    torch.cuda.synchronize()
+    sph.sph_profile_reset()
+    sph.sph_profile_select(None)
+    sph.sph_profile_enable(True)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sph.sph_nnps_query_half(g, rp, col, col.numel(), rho, sptr)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    sph.sph_profile_enable(False)
+    kern = {}
+    for tag in ("count", "scan", "fill", "sort"):
+        kms, c = sph.sph_profile_read(tag)
+        if c:
+            kern[tag] = kms / steps
+    sph.sph_grid_free(g)
+    t = sum(ms) / steps
+    return {"ms": t, "kernel_ms": kern, "tile_search_ms": full_search_ms,
+            "slower_than_tile_search": t / full_search_ms if full_search_ms else None,
+            "note": "each pair decided once (13 of 26 neighbour cells), written into both rows, rows sorted; "
+                    "fused density with atomic partner shares"}
 
 
 def bench_c3(sph, dev, stream, steps, peak, peak_src):

@@ -294,6 +294,21 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
 #define SPH_OPT_SM_SHARE 5
 int sph_grid_set_option(sph_grid_t grid, int option, int64_t value);
 
+/* The neighbour list over a half stencil: every pair decided once (from the
+ * particle whose cell comes first in (z, y, x) order, or in one cell from
+ * the lower sorted index, exactly as sph_nnps_query decides it) and written
+ * into both rows.  A count pass (with the density when rho != NULL, summed
+ * as sph_density_half sums it: an FP32 atomic adds the partner's share, so
+ * its last bits vary between calls), a scan, a fill pass at atomic row
+ * cursors and a per-row sort give the same CSR as sph_nnps_query (cell
+ * order).  Cell-order FP16-RCLL grids only; col == NULL counts only.
+ * Synchronises; SPH_ERR_CAPACITY (nothing written to col) when nnz exceeds
+ * col_capacity.  This is the symmetric "distance reuse" of the paper's
+ * conclusions applied to the full neighbour list; it is slower than
+ * sph_nnps_query on GB300 (see the measurement in the bench line). */
+int sph_nnps_query_half(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity, int64_t *nnz_out,
+                        float *rho, void *stream);
+
 /* Fill *info (host) with the grid's sizes and device pointers.  The pointers
  * stay valid until the grid is re-binned or freed. */
 int sph_grid_info_get(sph_grid_t grid, sph_grid_info *info);

@@ -460,6 +460,45 @@ extern "C" int sph_density_half(sph_grid_t grid, float *rho, void *stream) {
     return SPH_OK;
 }
 
+extern "C" int sph_nnps_query_half(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64_t col_capacity,
+                                   int64_t *nnz_out, float *rho, void *stream) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (!row_ptr) return fail(SPH_ERR_INVALID, "row_ptr is NULL");
+    if (g->p.precision != SPH_PREC_FP16_RCLL) return fail(SPH_ERR_INVALID, "FP16-RCLL grids only");
+    if (g->p.order != SPH_ORDER_CELL) return fail(SPH_ERR_INVALID, "cell-order grids only");
+    if (col && col_capacity < 0) return fail(SPH_ERR_INVALID, "negative col_capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    const long long n = g->n;
+    if (n == 0) {
+        SPH_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s));
+        SPH_CUDA(cudaStreamSynchronize(s));
+        if (nnz_out) *nnz_out = 0;
+        return SPH_OK;
+    }
+    const GridDev d = make_dev(g);
+    long long *rp = reinterpret_cast<long long *>(row_ptr);
+    SPH_CUDA(launch_status_reset_counters(P<DevStatus>(g->status), s));
+    SPH_TRY(ensure(g->rowcnt, n * sizeof(int), s));
+    SPH_CUDA(launch_half_count(d, P<int>(g->scell), P<int>(g->rowcnt), rho, g->sm_count, s));
+    SPH_CUDA(exclusive_scan_i64(P<int>(g->rowcnt), rp, n, g->scan_tmp.p, s));
+    long long nnz = 0;
+    SPH_TRY(read_nnz(g, rp, &nnz));
+    if (nnz_out) *nnz_out = nnz;
+    SPH_TRY(status_to_code(g->h_status->flags));
+    if (!col) return SPH_OK;
+    if (nnz > col_capacity)
+        return fail(SPH_ERR_CAPACITY, "nnz %lld exceeds col_capacity %lld", nnz, (long long)col_capacity);
+    SPH_TRY(ensure(g->tmp_rp, (size_t)(n + 1) * sizeof(long long), s));
+    SPH_CUDA(copy_d2d_kernel(g->tmp_rp.p, rp, (size_t)n * sizeof(long long), s));
+    SPH_CUDA(launch_half_fill(d, P<int>(g->scell), P<unsigned long long>(g->tmp_rp), col, g->sm_count, s));
+    SPH_CUDA(segmented_sort_rows(col, rp, n, P<int>(g->big_list), &P<DevStatus>(g->status)->big_cells, g->sm_count,
+                                 s));
+    SPH_TRY(read_status(g));
+    return status_to_code(g->h_status->flags);
+}
+
 extern "C" int sph_density_sum(sph_grid_t grid, const int64_t *row_ptr, const int32_t *col, float *rho,
                                void *stream) {
     sph_grid_s *g = grid;

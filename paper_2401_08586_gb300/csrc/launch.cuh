@@ -53,6 +53,12 @@ cudaError_t launch_canon(int n, const int *rank, const int *orig_id, const long 
 // Appendix Eq. A5 gradient over a CSR (gradient.cu); fs: float2 scratch of n.
 // Summation density over a half stencil, rho in sorted order (density_half.cu).
 cudaError_t launch_density_half(const GridDev &g, const int *scell, float *rho, int sm_count, cudaStream_t s);
+// Half-stencil CSR (density_half.cu): row lengths into cnt (zeroed here) and
+// the density (rho != NULL); then both entries of every pair at the row
+// cursors cur (a copy of the row starts), rows unsorted.
+cudaError_t launch_half_count(const GridDev &g, const int *scell, int *cnt, float *rho, int sm_count, cudaStream_t s);
+cudaError_t launch_half_fill(const GridDev &g, const int *scell, unsigned long long *cur, int *col, int sm_count,
+                             cudaStream_t s);
 cudaError_t launch_gradient_a5(const GridDev &g, const int *rank, const int *scell, const long long *row_ptr,
                                const int *col, int canonical, const double *f, float2 *fs, double *grad,
                                int sm_count, cudaStream_t s);

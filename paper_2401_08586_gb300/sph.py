@@ -139,6 +139,7 @@ def load(build_if_missing=False):
         "sph_grid_csr": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                          ctypes.POINTER(ctypes.c_int64)],
         "sph_grid_csr_copy": [_vp, _vp, _vp, _vp],
+        "sph_nnps_query_half": [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp, _vp],
         "sph_profile_enable": [ctypes.c_int],
         "sph_profile_reset": [],
         "sph_profile_select": [ctypes.c_char_p],
@@ -179,6 +180,7 @@ def exported_symbols():
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
             "sph_grid_export", "sph_grid_export_rel", "sph_density_half", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr", "sph_grid_csr_copy",
+            "sph_nnps_query_half",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
             "sph_advance", "sph_gradient_a5", "sph_precision_study", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
@@ -298,6 +300,14 @@ def sph_search_host(params, xyz_host, n, rho_host=None, stream=None, grid=None):
     _check(load().sph_search_host(ctypes.byref(params), _host_ptr(xyz_host), int(n), _host_ptr(rho_host),
                                   ctypes.byref(nnz), ctypes.byref(g), _stream(stream)))
     return g.value, nnz.value
+
+
+def sph_nnps_query_half(grid, row_ptr, col=None, col_capacity=0, rho=None, stream=None):
+    """Half-stencil neighbour list (include/sph.h); returns nnz."""
+    nnz = ctypes.c_int64(-1)
+    _check(load().sph_nnps_query_half(grid, _ptr(row_ptr), _ptr(col), int(col_capacity), ctypes.byref(nnz), _ptr(rho),
+                                      _stream(stream)))
+    return nnz.value
 
 
 def sph_grid_csr_copy(grid, row_ptr=None, col=None, stream=None):

@@ -359,3 +359,32 @@ def test_canonical_row_lengths(sph, dim, khr):
     check_against_oracle(out, xyz, h, 2 * h, 1)
     lens = np.diff(out["rp"])
     assert lens.max() > {2.4: 16, 4.0: 40, 2.6: 64, 3.6: 128, 4.6: 256}[khr]
+
+
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "random3d", "faces3d", "dambreak_small", "two"])
+def test_half_stencil_csr(sph, case):
+    """sph_nnps_query_half (each pair decided once, written into both rows,
+    rows sorted) gives the tile search's CSR exactly and the oracle's density
+    within the tolerance; its count-only call gives the same row pointers;
+    a short capacity is refused with nothing written."""
+    xyz, h = CASES[case]()
+    out = run(sph, xyz, h, 2 * h, 0)
+    g = out["grid"]
+    n = xyz.shape[0]
+    nnz = int(out["rp"][-1])
+    rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    assert sph.sph_nnps_query_half(g.handle, rp) == nnz
+    assert np.array_equal(rp.cpu().numpy(), out["rp"])
+    col = torch.full((nnz + 64,), -7, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.float32, device="cuda")
+    assert sph.sph_nnps_query_half(g.handle, rp, col, col.numel(), rho) == nnz
+    assert np.array_equal(rp.cpu().numpy(), out["rp"])
+    assert np.array_equal(col[:nnz].cpu().numpy(), out["col"])
+    half = dict(out, rho=rho.cpu().numpy())
+    check_against_oracle(half, xyz, h, 2 * h, 0)
+    if nnz > 0:
+        col2 = torch.full((nnz,), -7, dtype=torch.int32, device="cuda")
+        with pytest.raises(sph.SphError) as ei:
+            sph.sph_nnps_query_half(g.handle, rp, col2, nnz - 1)
+        assert ei.value.code == sph.SPH_ERR_CAPACITY
+        assert np.all(col2.cpu().numpy() == -7)
