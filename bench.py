@@ -113,7 +113,10 @@ def issue_per_clock(sm_count):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every SAMPLE_MS ms
+    from just before the timed region to just after it."""
+
+    SAMPLE_MS = 10
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -129,7 +132,7 @@ class ClockSampler:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "-lms", str(self.SAMPLE_MS)], stdout=self.tmp, stderr=subprocess.DEVNULL)
             # the timed region starts only once the sampler is producing rows
             t_end = time.time() + 10.0
             while time.time() < t_end and os.path.getsize(self.tmp.name) == 0 and self.proc.poll() is None:
@@ -440,6 +443,7 @@ def main():
         line["query_variants"] = bench_query_variants(sph, ps, xyz, dev, stream, max(3, min(args.steps, 20)))
         if args.workload == "3d_1m" and SIDE == 100:
             line["c3_8m"] = bench_c3(sph, dev, stream, max(3, min(args.steps, 10)), peak, peak_src)
+            line["c4_batch"] = bench_c4(sph, dev, stream, max(3, min(args.steps, 10)), peak, peak_src)
         line["e2e"] = bench_e2e(sph, ps, dev, stream, args)
         if world > 1:
             line["e2e"]["value"] = world * n * args.steps / replicas.max_over_ranks(line["e2e"]["seconds"], world,
@@ -514,6 +518,57 @@ def bench_fp64(sph, ps, xyz, dev, stream, steps, fp16_value, fp16_search_ms=None
     if fp16_search_ms and search_ms:
         out["search_speedup"] = search_ms / fp16_search_ms
     return out
+
+
+def bench_c4(sph, dev, stream, steps, peak, peak_src):
+    """The batched workload (C4: 256 independent 3D systems of 2e3..2e5
+    particles) through sph_batch_run: per run the bounds, then one replayed
+    CUDA graph (binning, tile list, persistent search); CUDA events per run,
+    the search launch timed in an untimed pass of direct launches."""
+    import torch
+    from paper_2401_08586_gb300 import workloads as W
+    systems = W.c4_batched()
+    xs = [torch.from_numpy(ps.xyz).to(dev) for ps in systems]
+    params = [sph.make_params(3, ps.h, ps.kh, order=sph.SPH_ORDER_CELL) for ps in systems]
+    ntot = sum(ps.n for ps in systems)
+    pairs = list(zip(xs, params))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    b = sph.Batch()
+    for _ in range(3):
+        flush.fill_(1.0)
+        b.run(pairs, stream=stream)
+    torch.cuda.synchronize()
+    st0 = b.stats()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rp, col, rho, orig, first = b.run(pairs, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+    st = b.stats()
+    nnz = int(rp[-1].item())
+    b.set_option(sph.SPH_BATCH_OPT_GRAPH, 0)
+    sph.sph_profile_reset()
+    sph.sph_profile_select("fused")
+    for k in range(3):
+        flush.fill_(float(k))
+        b.run(pairs, stream=stream)
+    torch.cuda.synchronize()
+    sph.sph_profile_enable(False)
+    fms, fc = sph.sph_profile_read("fused")
+    b.close()
+    t = sum(ms) / steps
+    launch = fms / max(fc, 1)
+    alg = ntot * (8 + 16 + 8 + 4) + 4 * nnz
+    return {"workload": BATCH_DESC, "n_particles": ntot, "systems": len(systems), "value": ntot / (t * 1e-3),
+            "unit": "particles/s", "ms_per_run": t, "steps": steps, "nnz": nnz,
+            "graph_replays": st.graph_replays - st0.graph_replays, "direct_launches_per_run": st.direct_launches,
+            "roofline": {"bound": "hbm", "kernel": "k_nnps_tile (batch)", "achieved": alg / (launch * 1e-3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": alg / (launch * 1e-3) / 1e9 / peak,
+                         "peak_source": peak_src, "launch_ms": launch, "algorithmic_bytes_per_launch": alg}}
 
 
 def bench_half_csr(sph, ps, xyz, dev, stream, steps, full_search_ms):
