@@ -109,14 +109,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// P(R) of Eq. 3 without alpha_d, branch-free: 2/3 - R^2 + R^3/2 on [0, 1),
-// (2 - R)^3 / 6 on [1, 2).  Only called for neighbours (R < 2); other values
-// are discarded by the caller.
-__device__ __forceinline__ float w_poly_bf(float R) {
-    const float t = 2.f - R;
-    const float w2 = t * t * t * (1.f / 6.f);
-    const float w1 = fmaf(R * R, fmaf(0.5f, R, -1.f), 2.f / 3.f);
-    return R < 1.f ? w1 : w2;
+// 6 P(R) of Eq. 3 (P without alpha_d) for 0 <= R < 2, without a branch:
+// (2 - R)^3 - 4 max(1 - R, 0)^3 equals (2 - R)^3 on [1, 2) and 4 - 6 R^2 +
+// 3 R^3 = 6 (2/3 - R^2 + R^3 / 2) on [0, 1); the clamp is a saturating add.
+// Only called for neighbours (R < 2); other values are discarded by the
+// caller.  The factor 1/6 is applied once per row.
+__device__ __forceinline__ float w_poly6(float R) {
+    const float t = 2.f - R, s = __saturatef(1.f - R);
+    return __fmaf_rn(-4.f * s, s * s, t * t * t);
 }
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -382,7 +382,7 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
     } else if (dens) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float wk = w_poly_bf(sqrt_approx(r2[k]) * g.r_scale);
+            const float wk = w_poly6(sqrt_approx(r2[k]) * g.r_scale);
             acc += in[k] ? wk : 0.f;
         }
     }
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(32 * C::WPB, C::WSM / C::WPB)
         if (col != nullptr && !wc && lane == 0) atomicOr(&g0.status->flags, ST_CAPACITY);
         if (mine) {
             row_ptr[h.i] = pre + rstart;
-            if (want_rho) rho[h.i] = g.w_norm * (2.f / 3.f + acc);
+            if (want_rho) rho[h.i] = g.w_norm * (2.f / 3.f + acc * (1.f / 6.f));
         }
         if (t == ntiles - 1 && lane == 0) row_ptr[g0.n] = pre + agg;
         if (!wc) continue;
