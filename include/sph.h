@@ -356,6 +356,28 @@ const char *sph_last_error(void);
 int sph_search_host(const sph_params *p, const double *xyz_host, int64_t n, float *rho_host,
                     int64_t *nnz_host, sph_grid_t *grid, void *stream);
 
+/* sph_search_host without the final wait, for callers that overlap
+ * consecutive searches (two grids on two streams: one search's copies run
+ * while the other's kernels do).  The call copies xyz in, bins (reading the
+ * bounds back waits for this stream's copy and bounds kernel only), searches
+ * with the grid's column buffer as it is, and queues the copy of the density
+ * to rho_host (pinned host memory) and of nnz into the grid's host record;
+ * it returns without waiting for them.  xyz_host and rho_host must stay
+ * valid until sph_search_host_finish.  The first call on a grid, or a call
+ * whose n or dim differs from the grid's last, runs sph_search_host instead
+ * (it sizes the column buffer and waits).  A call on a grid whose previous
+ * asynchronous search is unfinished finishes that one first. */
+int sph_search_host_async(const sph_params *p, const double *xyz_host, int64_t n, float *rho_host,
+                          int64_t *nnz_host, sph_grid_t *grid, void *stream);
+/* Wait for the grid's last sph_search_host_async; then nnz (here, or to the
+ * nnz_host given to that call when this one is NULL), the density and the CSR
+ * are complete.  SPH_ERR_CAPACITY when the neighbours outgrew the grid's
+ * column buffer (the CSR is then incomplete: call sph_search_host, which
+ * grows it); the status errors of sph_nnps_query otherwise.  When nothing
+ * is pending (the last call ran synchronously) it returns SPH_OK and that
+ * search's nnz. */
+int sph_search_host_finish(sph_grid_t grid, int64_t *nnz_host);
+
 /* Device pointers of the grid-owned CSR and density written by the last
  * sph_search_host on this grid (host out-pointers; any may be NULL). */
 /* Copy the CSR written by the last sph_search_host on this grid into caller

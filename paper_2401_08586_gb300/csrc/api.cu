@@ -44,6 +44,8 @@ struct sph_grid_s {
     double drift = 0;       // bound on |rel64 - conversion of xyz| in units of u
     long long own_nnz = 0;
     DevStatus *h_status = nullptr;  // pinned host mirror
+    bool async_pending = false;     // sph_search_host_async enqueued, sph_search_host_finish not yet called
+    int64_t *async_nnz = nullptr;   // where sph_search_host_finish reports nnz
 };
 
 static GridDev make_dev(sph_grid_s *g) {
@@ -676,6 +678,59 @@ extern "C" int sph_search_host(const sph_params *p, const double *xyz_host, int6
         SPH_CUDA(cudaMemcpyAsync(rho_host, g->own_rho.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
     SPH_CUDA(cudaStreamSynchronize(s));
     if (nnz_host) *nnz_host = nnz;
+    return SPH_OK;
+}
+
+extern "C" int sph_search_host_async(const sph_params *p, const double *xyz_host, int64_t n, float *rho_host,
+                                     int64_t *nnz_host, sph_grid_t *grid, void *stream) {
+    if (!grid) return fail(SPH_ERR_INVALID, "grid is NULL");
+    SPH_TRY(validate_params(p, n, xyz_host));
+    sph_grid_s *g = *grid;
+    // the first call on a grid (or one with a different shape) sizes the
+    // grid-owned CSR: the synchronous form does that and leaves nothing pending
+    if (g == nullptr || g->async_pending || !g->own_col.p || g->n != n || g->p.dim != p->dim) {
+        if (g && g->async_pending) SPH_TRY(sph_search_host_finish(g, nullptr));
+        return sph_search_host(p, xyz_host, n, rho_host, nnz_host, grid, stream);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    if (n > 0) SPH_CUDA(cudaMemcpyAsync(g->own_xyz.p, xyz_host, (size_t)n * p->dim * sizeof(double),
+                                        cudaMemcpyHostToDevice, s));
+    // binning reads the bounds back (this waits for the copy and the bounds
+    // kernel of this stream only); the search then runs with the grid's column
+    // capacity and no host read; the density and the status record (with nnz)
+    // come back asynchronously
+    SPH_TRY(sph_bin_cells(p, P<double>(g->own_xyz), n, stream, grid));
+    const long long cap = (long long)(g->own_col.cap / sizeof(int));
+    SPH_TRY(sph_nnps_query(g, P<int64_t>(g->own_rp), P<int32_t>(g->own_col), cap, nullptr, P<float>(g->own_rho),
+                           stream));
+    if (rho_host && n > 0)
+        SPH_CUDA(cudaMemcpyAsync(rho_host, g->own_rho.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(status_to_host(g->h_status, P<DevStatus>(g->status), P<long long>(g->own_rp) + n, s));
+    g->async_pending = true;
+    g->async_nnz = nnz_host;
+    return SPH_OK;
+}
+
+extern "C" int sph_search_host_finish(sph_grid_t grid, int64_t *nnz_host) {
+    sph_grid_s *g = grid;
+    if (!g) return fail(SPH_ERR_INVALID, "grid is NULL");
+    if (!g->async_pending) {
+        // nothing queued (the last call ran synchronously): its nnz
+        if (nnz_host) *nnz_host = g->own_nnz;
+        return SPH_OK;
+    }
+    g->async_pending = false;
+    SPH_CUDA(cudaStreamSynchronize(g->stream));
+    const long long nnz = g->h_status->nnz;
+    int64_t *out = nnz_host ? nnz_host : g->async_nnz;
+    if (out) *out = nnz;
+    g->own_nnz = nnz;
+    if (g->n > 0) g->last_nbr = (double)nnz / (double)g->n;
+    int rc = status_to_code(g->h_status->flags & ~(unsigned)ST_CAPACITY);
+    if (rc != SPH_OK) return rc;
+    if (nnz > (long long)(g->own_col.cap / sizeof(int)))
+        return fail(SPH_ERR_CAPACITY, "nnz %lld exceeds the grid's column buffer: call sph_search_host", nnz);
     return SPH_OK;
 }
 

@@ -140,6 +140,9 @@ def load(build_if_missing=False):
                          ctypes.POINTER(ctypes.c_int64)],
         "sph_grid_csr_copy": [_vp, _vp, _vp, _vp],
         "sph_nnps_query_half": [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp, _vp],
+        "sph_search_host_async": [ctypes.POINTER(sph_params), _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(_vp), _vp],
+        "sph_search_host_finish": [_vp, ctypes.POINTER(ctypes.c_int64)],
         "sph_profile_enable": [ctypes.c_int],
         "sph_profile_reset": [],
         "sph_profile_select": [ctypes.c_char_p],
@@ -180,7 +183,7 @@ def exported_symbols():
     return ["sph_bin_cells", "sph_nnps_query", "sph_density_sum", "sph_grid_info_get",
             "sph_grid_export", "sph_grid_export_rel", "sph_density_half", "sph_grid_check", "sph_grid_free", "sph_last_error",
             "sph_precision_bands", "sph_version", "sph_search_host", "sph_grid_csr", "sph_grid_csr_copy",
-            "sph_nnps_query_half",
+            "sph_nnps_query_half", "sph_search_host_async", "sph_search_host_finish",
             "sph_profile_enable", "sph_profile_select", "sph_profile_reset", "sph_profile_read",
             "sph_launch_count", "sph_grid_set_option", "sph_nnps_query_static", "sph_device_fp64_rate",
             "sph_advance", "sph_gradient_a5", "sph_precision_study", "sph_batch_create", "sph_batch_run", "sph_batch_get_stats", "sph_batch_set_option", "sph_batch_free",
@@ -314,6 +317,22 @@ def sph_grid_csr_copy(grid, row_ptr=None, col=None, stream=None):
     """Copy the grid-owned CSR of the last sph_search_host into row_ptr / col
     (pinned CPU or CUDA tensors, or host numpy arrays); synchronises."""
     _check(load().sph_grid_csr_copy(grid, _host_ptr(row_ptr), _host_ptr(col), _stream(stream)))
+
+
+def sph_search_host_async(params, xyz_host, n, rho_host=None, stream=None, grid=None):
+    """Queue a host-buffer search (include/sph.h); returns the grid handle.
+    xyz_host / rho_host must stay alive until sph_search_host_finish."""
+    g = _vp(grid)
+    _check(load().sph_search_host_async(ctypes.byref(params), _host_ptr(xyz_host), int(n), _host_ptr(rho_host), None,
+                                        ctypes.byref(g), _stream(stream)))
+    return g.value
+
+
+def sph_search_host_finish(grid):
+    """Wait for the grid's queued host-buffer search; returns nnz."""
+    nnz = ctypes.c_int64(-1)
+    _check(load().sph_search_host_finish(grid, ctypes.byref(nnz)))
+    return nnz.value
 
 
 def sph_grid_csr(grid):

@@ -388,3 +388,60 @@ def test_half_stencil_csr(sph, case):
             sph.sph_nnps_query_half(g.handle, rp, col2, nnz - 1)
         assert ei.value.code == sph.SPH_ERR_CAPACITY
         assert np.all(col2.cpu().numpy() == -7)
+
+
+@pytest.mark.parametrize("share", [100, 40, 1])
+def test_sm_share_same_result(sph, share):
+    """SPH_OPT_SM_SHARE only sizes the persistent grid: the CSR and the
+    density bits are those of the full grid, down to one CTA."""
+    xyz, h = CASES["lattice3d_27k"]()
+    full = run(sph, xyz, h, 2 * h, 0)
+    x = torch.from_numpy(np.ascontiguousarray(xyz)).cuda()
+    g = sph.Grid(x, h, 2 * h)
+    sph.sph_grid_set_option(g.handle, sph.SPH_OPT_SM_SHARE, share)
+    rp, col, rho = g.query(density=True)
+    assert np.array_equal(rp.cpu().numpy(), full["rp"])
+    assert np.array_equal(col.cpu().numpy(), full["col"])
+    assert np.array_equal(rho.cpu().numpy(), full["rho"])
+    with pytest.raises(sph.SphError):
+        sph.sph_grid_set_option(g.handle, sph.SPH_OPT_SM_SHARE, 0)
+
+
+def test_search_host_async_matches_sync(sph):
+    """sph_search_host_async / _finish on two grids and two streams give the
+    synchronous call's density, nnz and CSR; a set whose neighbours outgrow
+    the grid's column buffer is reported by _finish as SPH_ERR_CAPACITY and
+    the synchronous call then grows the buffer."""
+    xyz, h = CASES["lattice3d_27k"]()
+    n = xyz.shape[0]
+    params = sph.make_params(3, h, 2 * h, order=sph.SPH_ORDER_CELL)
+    xh = torch.from_numpy(np.ascontiguousarray(xyz)).pin_memory()
+    rho_ref = torch.empty(n, dtype=torch.float32).pin_memory()
+    g_ref, nnz_ref = sph.sph_search_host(params, xh, n, rho_ref, None, None)
+    rp_ref = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    col_ref = torch.empty(nnz_ref, dtype=torch.int32).pin_memory()
+    sph.sph_grid_csr_copy(g_ref, rp_ref, col_ref)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    rhos = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(2)]
+    gs = [None, None]
+    for rnd in range(3):
+        for b in range(2):
+            gs[b] = sph.sph_search_host_async(params, xh, n, rhos[b], streams[b].cuda_stream, gs[b])
+        for b in range(2):
+            assert sph.sph_search_host_finish(gs[b]) == nnz_ref
+            assert torch.equal(rhos[b], rho_ref)
+            rp = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+            col = torch.empty(nnz_ref, dtype=torch.int32).pin_memory()
+            sph.sph_grid_csr_copy(gs[b], rp, col)
+            assert torch.equal(rp, rp_ref) and torch.equal(col, col_ref)
+    # a denser set of the same size: the grid's column buffer is too small
+    dense = sph.make_params(3, 1.6 * h, 3.2 * h, order=sph.SPH_ORDER_CELL)
+    sph.sph_search_host_async(dense, xh, n, rhos[0], streams[0].cuda_stream, gs[0])
+    with pytest.raises(sph.SphError) as ei:
+        sph.sph_search_host_finish(gs[0])
+    assert ei.value.code == sph.SPH_ERR_CAPACITY
+    _, nnz_dense = sph.sph_search_host(dense, xh, n, rhos[0], None, gs[0])
+    rp_o, col_o = oracle.cll(xyz, 3.2 * h)
+    assert nnz_dense == col_o.size
+    for g in gs + [g_ref]:
+        sph.sph_grid_free(g)

@@ -95,6 +95,20 @@ def test_static_query_refuses_oversized_grids(sph):
     g.close()
 
 
+def test_static_query_dense_set(sph):
+    """A lattice with ~140 neighbours per particle: the grid's tile choice is
+    the dense shape, which the no-allocation call takes over."""
+    xyz = W.lattice((36, 36, 36), 1.0 / 36, 0.1, seed=17)
+    h = 1.6 / 36
+    g = sph.Grid(torch.from_numpy(xyz).cuda(), h, 2 * h)
+    ref = regular(sph, g)
+    assert ref[0][-1] / g.n > 110
+    cap = int(ref[0][-1])
+    same(static_call(sph, g, cap), ref)
+    same(static_call(sph, g, cap), ref)
+    g.close()
+
+
 def thin_slab(n, seed):
     """Uniform random particles in a 0.05 x 1.5 x 1.5 slab: with kh = 0.01 the
     grid has 5 x 150 x 150 cells, i.e. 22,500 rows of cells."""
