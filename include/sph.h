@@ -272,10 +272,9 @@ int sph_nnps_query_static(sph_grid_t grid, int64_t *row_ptr, int32_t *col, int64
  *     chosen from the neighbours per particle, 0 sparse (up to 672 kept
  *     candidates per pass of a tile, 20 resident warps per SM, output staged
  *     for tiles of up to ~80 neighbours per row), 1 dense (832 kept
- *     candidates, 16 warps), 2 whole-pass (512 kept candidates, FP32
- *     coordinates of all of them staged so each lane walks its bits once per
- *     tile, 18 warps).  Same CSR either way; the density's last bits follow
- *     the summation order of the shape. */
+ *     candidates, 16 warps); other values are refused (SPH_ERR_INVALID).
+ *     Same CSR and the same density bits either way: every row's Eq. 3 sum
+ *     adds its pairs in column order whatever the shape. */
 #define SPH_OPT_TILE_SHAPE 3
 /*   SPH_OPT_TEST_LOOKBACK: for tests of the bounded device waits only.  0
  *     (default): normal queries.  k in 1 .. 2^20: the next queries run the

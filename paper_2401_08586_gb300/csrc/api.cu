@@ -616,7 +616,7 @@ extern "C" int sph_grid_set_option(sph_grid_t grid, int option, int64_t value) {
         return SPH_OK;
     }
     if (option == SPH_OPT_TILE_SHAPE) {
-        if (value < -1 || value > 2) return fail(SPH_ERR_INVALID, "SPH_OPT_TILE_SHAPE takes -1, 0, 1 or 2");
+        if (value < -1 || value > 1) return fail(SPH_ERR_INVALID, "SPH_OPT_TILE_SHAPE takes -1, 0 or 1");
         g->tile_shape = (int)value;
         return SPH_OK;
     }

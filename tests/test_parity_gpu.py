@@ -318,6 +318,32 @@ def test_tile_shapes_and_staging(sph, case, shape, staging):
     check_against_oracle(out, xyz, h, 2 * h, 0)
 
 
+@pytest.mark.parametrize("case", ["c1_2d_10k", "lattice3d_27k", "random3d_dense", "lattice3d_wide"])
+def test_density_bits_independent_of_tile_shape(sph, case):
+    """The two shared-memory shapes cut the kept candidates into windows of
+    192 and 256 (and passes of 672 and 832) and batch the walk's bits
+    differently; each row's Eq. 3 sum still adds its pairs in candidate order,
+    one weight per pair computed the same way in every batch slot, so the
+    densities agree bit for bit, and the lists are the same."""
+    if case == "random3d_dense":
+        xyz, h = W.random_uniform(20000, 3, 21), 0.05
+    elif case == "lattice3d_wide":
+        xyz, h = W.c2_3d_1m(side=24).xyz, 0.016
+    else:
+        xyz, h = CASES[case]()
+    x = torch.from_numpy(np.ascontiguousarray(xyz)).cuda()
+    res = []
+    for shape in (0, 1):
+        g = sph.Grid(x, h, 2 * h, order=0)
+        sph.sph_grid_set_option(g.handle, sph.SPH_OPT_TILE_SHAPE, shape)
+        rp, col, rho = g.query()
+        res.append((rp.cpu().numpy(), col.cpu().numpy(), rho.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
+    with pytest.raises(sph.SphError):
+        sph.sph_grid_set_option(g.handle, sph.SPH_OPT_TILE_SHAPE, 2)
+
+
 @pytest.mark.parametrize("dim,n,h", [(3, 200000, 0.0025), (2, 300000, 0.0001)])
 def test_large_sparse_grid(sph, dim, n, h):
     """A sparse set over a fine grid (8M cells in 3D, 25M in 2D): the
