@@ -16,14 +16,19 @@
 //   * cull: candidates farther than kh (plus a margin) from the bounding box
 //     of the group's particles cannot be anybody's neighbour and are dropped;
 //     the rest are compacted in candidate order (ascending column);
-//   * stage a window of kept candidates in shared memory, two per half2 word;
+//   * stage windows of kept candidates in shared memory: FP16 coordinates
+//     two per half2 word for the window's test, FP32 coordinates into a
+//     ring that holds two windows;
 //   * FP16 test (all lanes, candidates broadcast): e = ((dx^2 - T) + dy^2)
 //     + dz^2 with half2 FMAs; e < tau16 sets the candidate's bit in the
 //     lane's row bitmask;
 //   * each lane walks its own bits: FP32 distance from the FP32 relative
 //     coordinates, FP32 band decision (FP64 definition inside the band),
 //     neighbour count and density sum (Eq. 3) in CSR order; rejected bits are
-//     cleared.
+//     cleared.  Window w is walked once window w + 1 is staged and tested, so
+//     a lane that has finished its bits of w goes on with its bits of w + 1
+//     while the others finish w (the lanes' bit counts differ per window far
+//     more than per tile).
 // Then the tile's neighbour total is published and its CSR offset found by a
 // decoupled look-back over earlier tiles; each lane writes its row pointer
 // and density, and emits its row from the kept bits.  Tiles with several
@@ -53,22 +58,30 @@ constexpr float CULL_MARGIN = 0.02f;  // u^2, covers the FP16 rounding of the cu
 constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch may ask for
 
 // Shared-memory shape of the tile search: kept candidates per pass (the
-// bitmask length), per staging window, warps per CTA and the resident warps
-// per SM it is built for (the register budget: 96 per thread at 20 warps,
-// 128 at 16), and the walk's bits in flight per lane (measured: 3 at 20
-// warps, 4 at 16).  Each warp works alone on its own tiles in its own
-// shared-memory area; two warps per CTA share the SM's per-CTA reservation.
-// Sparse: 10.8 KB per warp, 20 warps per SM; its output area (code, pw and
-// f32 after the last window) holds 2,640 entries, a tile of 32 rows of up to
-// ~80 neighbours.  Dense: 13.7 KB, 16 warps, 832 kept candidates and 3,488
-// output entries for denser particle sets.
-template <int CMAX_, int WIN_, int WPB_, int WSM_, int WB_>
+// bitmask length), candidates per staging window, windows whose FP32
+// coordinates stay staged together (a ring: the walk of window w may run
+// into window w + 1 while the slowest lane finishes w), warps per CTA and the
+// resident warps per SM it is built for (the register budget: 96 per thread
+// at 20 warps, 128 at 16), the walk's bits in flight per lane (measured: 3 at
+// 20 warps, 4 at 16) and spare bytes that only widen the output staging area.
+// Each warp works alone on its own tiles in its own shared-memory area; two
+// warps per CTA share the SM's per-CTA reservation.  Sparse: 10.8 KB per
+// warp, 20 warps per SM; its output area (code, pw, the FP32 ring and the
+// spare bytes after the last window) holds 2,640 entries, a tile of 32 rows
+// of up to ~80 neighbours.  Dense: 13.7 KB, 16 warps, 832 kept candidates and
+// 3,488 output entries for denser particle sets.
+template <int CMAX_, int WIN_, int NBUF_, int WPB_, int WSM_, int WB_, int SPARE_>
 struct TileCfg {
     static constexpr int CMAX = CMAX_;
     static constexpr int WIN = WIN_;
+    static constexpr int NBUF = NBUF_;
+    static constexpr int RING = NBUF_ * WIN_;  // FP32 slots of the ring
+    static constexpr int RW = RING / 32;        // ring words: kept word q is staged at ring word q % RW
+    static constexpr int WW = WIN_ / 32;        // words per window
     static constexpr int WPB = WPB_;
     static constexpr int WSM = WSM_;
     static constexpr int WB = WB_;  // bits in flight per lane in the walk (independent loads and arithmetic)
+    static constexpr int SPARE = SPARE_;
     static constexpr int NWORD = CMAX_ / 32;
     // Bitmask matrix: NWORD + 1 words per lane.  With an even row stride the
     // words of lanes l and l + 16 in one column share a bank; lanes 16..31
@@ -76,10 +89,12 @@ struct TileCfg {
     // lanes' words of a column in 32 different banks.
     static constexpr int SSHIFT = (NWORD + 1) % 2 == 0 ? 1 : 0;
     static_assert(CMAX_ % 32 == 0 && WIN_ % 32 == 0 && WIN_ <= CMAX_, "tile shape");
+    static_assert(NBUF_ == 2, "the walk of a window runs into the next one only");
+    static_assert(NWORD <= 32, "non-empty word masks are 32 bits");
     static_assert(WSM_ % WPB_ == 0, "warps per CTA");
 };
-using TileSparse = TileCfg<672, 192, 2, 20, 3>;
-using TileDense = TileCfg<832, 256, 2, 16, 4>;
+using TileSparse = TileCfg<672, 128, 2, 2, 20, 4, 480>;
+using TileDense = TileCfg<832, 192, 2, 2, 16, 4, 16>;
 
 
 template <class C>
@@ -93,13 +108,18 @@ struct TileSmem {
     // code bits (dy + 1) << 3 | (dz + 1) << 5, frame shifts 2 dy and 2 dz (float bits)
     int4 rt[9];
     int rcum[10], pad[2];  // flat index of row r's first candidate; [nrows] = total
-    // code, pw and f32 come last and are contiguous with any extra dynamic
-    // shared memory of the launch: after the last window they hold the tile's
-    // staged output (16-bit kept-candidate slots), stg_slots of them
+    // code, pw, the ring and spare come last and are contiguous with any
+    // extra dynamic shared memory of the launch: after the last window they
+    // hold the tile's staged output (16-bit kept-candidate slots), stg_slots
+    // of them
     unsigned char code[C::CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5
-    uint4 pw[C::WIN / 2];         // FP16 pairs: word (g*16 + b) = kept candidates 32g + b (lo), 32g + 16 + b (hi)
-    float4 f32[C::WIN];           // FP32 frame coordinates, candidate index j in .w
-    static constexpr size_t staging_bytes() { return sizeof(code) + sizeof(pw) + sizeof(f32); }
+    uint4 pw[C::WIN / 2];         // FP16 pairs of the window under test: word (g*16 + b) = its candidates 32g + b (lo), 32g + 16 + b (hi)
+    float2 fxy[C::RING + 2];      // FP32 frame coordinates of the staged windows: kept slot 32 q + b at 32 (q % RW) + b,
+    float fz[C::RING + 4];        // then a guard slot (read, never used, by the walk's empty bits)
+    unsigned char spare[C::SPARE > 0 ? C::SPARE : 16];
+    static constexpr size_t staging_bytes() {
+        return sizeof(code) + sizeof(pw) + sizeof(fxy) + sizeof(fz) + sizeof(spare);
+    }
 };
 
 
@@ -217,15 +237,16 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
     return kept;
 }
 
-// Stage kept candidates [w0, w0 + wc) into the window (slots past wc padded
-// far away).
+// Stage kept candidates [w0, w0 + wc) (w0 a multiple of 32): FP16 pairs for
+// the window's test (slots past wc padded far away) and FP32 coordinates
+// into the ring at 32 (w0 / 32 % RW) + k.
 template <class C>
 __device__ __forceinline__ void stage_window(TileSmem<C> &S, const GridDev &g, int w0, int wc) {
     const int lane = threadIdx.x & 31;
+    const int ring0 = ((w0 >> 5) % C::RW) * 32;
 #pragma unroll 4
     for (int k = lane; k < C::WIN; k += 32) {
         __half hx, hy, hz;
-        float4 f;
         if (k < wc) {
             const int j = S.jall[w0 + k];
             const unsigned int c = S.code[w0 + k];
@@ -238,12 +259,11 @@ __device__ __forceinline__ void stage_window(TileSmem<C> &S, const GridDev &g, i
             hx = __low2half(xy);
             hy = __high2half(xy);
             hz = __hadd(__low2half(as_h2(q16.y)), __float2half_rn(sz));
-            f = make_float4(__fadd_rn(r32.x, sx), __fadd_rn(r32.y, sy), __fadd_rn(r32.z, sz), __int_as_float(j));
+            S.fxy[ring0 + k] = make_float2(__fadd_rn(r32.x, sx), __fadd_rn(r32.y, sy));
+            S.fz[ring0 + k] = __fadd_rn(r32.z, sz);
         } else {
             hx = hy = hz = __float2half_rn(30000.f);
-            f = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
         }
-        S.f32[k] = f;
         const int word = ((k >> 5) << 4) + (k & 15), hi = (k >> 4) & 1;
         __half *pw = reinterpret_cast<__half *>(&S.pw[word]);
         pw[hi] = hx;
@@ -258,7 +278,7 @@ __device__ __forceinline__ void stage_window(TileSmem<C> &S, const GridDev &g, i
 // own particle (window slot self_slot, or -1) is left out.
 template <int DIM, class C>
 __device__ __forceinline__ unsigned int test_window(TileSmem<C> &S, const Home &h, bool active, unsigned int negT,
-                                                    unsigned int tau, int wbase, int nwin, int self_slot) {
+                                                    unsigned int tau, int wbase, int nwin, int self_slot, int &nbits) {
     const int lane = threadIdx.x & 31;
     const __half2 nT = as_h2(negT);
     const __half2 tv = as_h2(tau);
@@ -283,6 +303,7 @@ __device__ __forceinline__ unsigned int test_window(TileSmem<C> &S, const Home &
         word = active ? word : 0u;
         S.bits(lane, wbase + gi) = word;
         nem |= (word != 0u ? 1u : 0u) << gi;
+        nbits += __popc(word);
     }
     __syncwarp();
     return nem;
@@ -290,40 +311,46 @@ __device__ __forceinline__ unsigned int test_window(TileSmem<C> &S, const Home &
 
 enum { PASS_COUNT = 0, PASS_EMIT = 1 };
 
-// Walk the lane's bits in words [wbase, wbase + nw) of the window: FP32
-// re-decision (FP64 inside the band) and density; rejected bits cleared.
-// PASS_EMIT writes the neighbours to col[rp + cnt] instead of summing.
-// The lane's set bits of words [wbase, wbase + nw) in ascending order, up to
-// WB per call: positions p[k] (window-local candidate slots) with v[k]
-// marking valid ones (v[0] false: no bits left).  State: the current word w
-// (its index gi), the next non-empty word wn (index gn), prefetched once per
-// call, and nem, the lane's non-empty words not yet fetched (bit q for word
-// wbase + q).  A word that runs out mid-call is replaced by a register move;
-// a call may return fewer than WB bits when two words run out in it, unless
-// EACH (refill before every bit: for long calls).
+// The lane's set bits in ascending order, up to WB per call: positions p[k]
+// with v[k] marking valid ones (invalid ones still index inside the row's
+// ring word or slot word, or one past it).  RING: p is the FP32 ring
+// position 32 (q % RW) + b of bit b of kept word q, else the kept slot
+// 32 q + b.  State: the current word w (its base rb), the next non-empty word
+// wn (base rbn), prefetched once per call, and nem, the lane's non-empty
+// words not yet fetched (bit q for word q).  A word that runs out mid-call is
+// replaced by a register move; the next word is prefetched before bits k
+// with k % RI == 0, so a call may return fewer than WB bits when two words
+// run out between prefetches.
 struct BitCursor {
     unsigned int w = 0u, wn = 0u, nem = 0u;
-    int gi = 0, gn = 0;
+    int rb = 0, rbn = 0;
 };
-template <int WB, class C, bool EACH = false>
-__device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, int wbase, BitCursor &b, int (&p)[WB],
-                                          bool (&v)[WB]) {
+template <int WB, class C, bool RING, int RI = WB>
+__device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, BitCursor &b, int (&p)[WB], bool (&v)[WB]) {
 #pragma unroll
     for (int k = 0; k < WB; ++k) {
-        if ((k == 0 || EACH) && b.wn == 0u && b.nem != 0u) {
-            b.gn = __ffs(b.nem) - 1;
+        if (k % RI == 0 && b.wn == 0u && b.nem != 0u) {
+            const int gn = __ffs(b.nem) - 1;
             b.nem &= b.nem - 1u;
-            b.wn = S.bits(lane, wbase + b.gn);
+            b.wn = S.bits(lane, gn);
+            b.rbn = RING ? (gn % C::RW) * 32 : gn * 32;
         }
         if (b.w == 0u) {
             b.w = b.wn;
-            b.gi = b.gn;
+            b.rb = b.rbn;
             b.wn = 0u;
         }
         v[k] = b.w != 0u;
-        p[k] = b.gi * 32 + (__ffs(b.w) - 1);
+        p[k] = b.rb + __clz(__brev(b.w));  // lowest set bit; 32 for an empty word
         b.w &= b.w - 1u;
     }
+}
+
+// Kept word of ring position p while windows from word q0 on are staged
+// (the ring holds the RW consecutive kept words from q0).
+template <class C>
+__device__ __forceinline__ int ring_word(int p, int q0) {
+    return q0 + ((p >> 5) - q0 % C::RW + C::RW) % C::RW;
 }
 
 
@@ -338,47 +365,44 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 
 // The lane's own particle has been removed from its bits by test_window, so
 // every remaining bit is a pair j != i.  The common case (FP32 says
-// "neighbour") runs without branches; pairs the FP32 tier rejects or leaves
-// in its band go through a warp-uniform slow path.  K bits (window-local
-// slots p[k], valid v[k]) of the lane's row.
+// "neighbour") runs without branches; a pair the FP32 tier rejects or leaves
+// in its band takes a per-lane branch (FP64 tier out of line; a rejected bit
+// is cleared).  K bits (ring positions p[k], valid v[k]) of the lane's row;
+// q0: first kept word still staged.
 template <int DIM, int PASS, class C, int K>
-__device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase,
+__device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int q0,
                                           const int (&p)[K], const bool (&v)[K], int &cnt, float &acc, int *col,
                                           long long rp, unsigned int &n32, unsigned int &n64, bool dens) {
     const int lane = threadIdx.x & 31;
     float r2[K];
-    int jj[K];
     bool in[K];
-    bool odd = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float4 c = S.f32[v[k] ? p[k] : 0];
-        jj[k] = __float_as_int(c.w);
-        const float d0 = __fsub_rn(c.x, h.x32);
-        const float d1 = __fsub_rn(c.y, h.y32);
-        const float d2 = __fsub_rn(c.z, h.z32);
+        const float2 cxy = S.fxy[p[k]];  // p[k] <= RING: invalid bits read the guard slot at worst
+        const float cz = S.fz[p[k]];
+        const float d0 = __fsub_rn(cxy.x, h.x32);
+        const float d1 = __fsub_rn(cxy.y, h.y32);
+        const float d2 = __fsub_rn(cz, h.z32);
         r2[k] = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
         in[k] = v[k] && r2[k] < g.t32_in;
-        odd |= v[k] && !in[k];
     }
-    if (__any_sync(0xffffffffu, odd)) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (v[k] && !in[k]) {
-                if (r2[k] <= g.t32_out) {
-                    ++n64;
-                    in[k] = fp64_tier<DIM>(g, h.i, jj[k]);
-                } else {
-                    ++n32;
-                }
-                if (!in[k]) S.bits(lane, wbase + (p[k] >> 5)) &= ~(1u << (p[k] & 31));
+    for (int k = 0; k < K; ++k) {
+        if (v[k] && !in[k]) {
+            const int q = ring_word<C>(p[k], q0);
+            if (r2[k] <= g.t32_out) {
+                ++n64;
+                in[k] = fp64_tier<DIM>(g, h.i, S.jall[q * 32 + (p[k] & 31)]);
+            } else {
+                ++n32;
             }
+            if (!in[k]) S.bits(lane, q) &= ~(1u << (p[k] & 31));
         }
     }
     if (PASS == PASS_EMIT) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (in[k]) col[rp + cnt++] = jj[k];
+            if (in[k]) col[rp + cnt++] = S.jall[ring_word<C>(p[k], q0) * 32 + (p[k] & 31)];
     } else if (dens) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -388,27 +412,23 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
     }
 }
 
-// Walk the lane's bits of one window in candidate order (the emit pass
-// needs it: columns ascending).
+// Walk the lane's bits in candidate order (the emit pass needs it: columns
+// ascending) until every lane has taken `target` bits (all its bits of the
+// windows before the current one; `taken` counts them); lanes that are done
+// run on into the next staged window.  q0: first kept word still staged.
 template <int DIM, int PASS, class C>
-__device__ __forceinline__ void walk_window(TileSmem<C> &S, const GridDev &g, const Home &h, int wbase, int nwin,
-                                            unsigned int nem, int &cnt, float &acc, int *col, long long rp,
-                                            unsigned int &n32, unsigned int &n64, bool dens) {
+__device__ __forceinline__ void walk_until(TileSmem<C> &S, const GridDev &g, const Home &h, BitCursor &cur, int q0,
+                                           int target, int &taken, int &cnt, float &acc, int *col, long long rp,
+                                           unsigned int &n32, unsigned int &n64, bool dens) {
     const int lane = threadIdx.x & 31;
-    BitCursor cur;
-    cur.nem = nem;
-    while (true) {
+    while (__any_sync(0xffffffffu, taken < target)) {
         int p[C::WB];
         bool v[C::WB];
-        next_bits<C::WB, C>(S, lane, wbase, cur, p, v);
-        if (!__any_sync(0xffffffffu, v[0])) break;
-        walk_bits<DIM, PASS, C, C::WB>(S, g, h, wbase, p, v, cnt, acc, col, rp, n32, n64, dens);
+        next_bits<C::WB, C, true>(S, lane, cur, p, v);
+#pragma unroll
+        for (int k = 0; k < C::WB; ++k) taken += v[k] ? 1 : 0;
+        walk_bits<DIM, PASS, C, C::WB>(S, g, h, q0, p, v, cnt, acc, col, rp, n32, n64, dens);
     }
-    if (PASS == PASS_COUNT) {
-        // the neighbours of this window: its bits that survived the re-decision
-        for (int q = 0; q < nwin; ++q) cnt += __popc(S.bits(lane, wbase + q));
-    }
-    __syncwarp();
 }
 
 // Set up a home group of lanes [gs, ge): frame, bounding box, band, rows.
@@ -445,6 +465,10 @@ __device__ __forceinline__ void group_setup(TileSmem<C> &S, const GridDev &g, Ho
 
 // All candidates of one group against its lanes; returns false when the kept
 // list needed more than one pass (the bits in S then cover only the last).
+// Per pass: window 0 is staged and tested; then for each window w the next
+// one is staged and tested (its FP32 coordinates go to the other half of the
+// ring, whose previous window every lane has finished) and the lanes walk
+// until all of them are past window w.
 template <int DIM, int PASS, class C>
 __device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home &h, bool act, const Group &G,
                                           float cullT, int &cnt, float &acc, int *col, long long rp,
@@ -456,14 +480,31 @@ __device__ __forceinline__ bool run_group(TileSmem<C> &S, const GridDev &g, Home
         kept = cull_fill<DIM, C>(S, g, G, cullT, cur, p0, nhome);
         ++passes;
         const int sp = S.selfpos[lane];
-        for (int w0 = 0; w0 < kept; w0 += C::WIN) {
-            const int wc = min(C::WIN, kept - w0);
-            stage_window<C>(S, g, w0, wc);
-            const int nwin = (wc + 31) >> 5;
-            const int self_slot = (sp >= w0 && sp < w0 + wc) ? sp - w0 : -1;
-            const unsigned int nem = test_window<DIM, C>(S, h, act, g.neg_t16, G.tau, w0 >> 5, nwin, self_slot);
-            walk_window<DIM, PASS, C>(S, g, h, w0 >> 5, nwin, nem, cnt, acc, col, rp, n32, n64, dens);
+        const int nwords = (kept + 31) >> 5;
+        BitCursor bc;
+        int tested = 0, taken = 0;  // the lane's bits in the windows tested so far, and taken by the walk
+        for (int w0 = 0; w0 < kept + C::WIN; w0 += C::WIN) {
+            // stage and test window w0 (if any), then walk window w0 - WIN
+            const int before = tested;
+            if (w0 < kept) {
+                const int wc = min(C::WIN, kept - w0);
+                stage_window<C>(S, g, w0, wc);
+                const int self_slot = (sp >= w0 && sp < w0 + wc) ? sp - w0 : -1;
+                bc.nem |= test_window<DIM, C>(S, h, act, g.neg_t16, G.tau, w0 >> 5, (wc + 31) >> 5, self_slot,
+                                              tested)
+                          << (w0 >> 5);
+            }
+            if (w0 > 0) {
+                const int q0 = (w0 - C::WIN) >> 5;  // first word still staged
+                walk_until<DIM, PASS, C>(S, g, h, bc, q0, w0 < kept ? before : tested, taken, cnt, acc, col, rp,
+                                         n32, n64, dens);
+            }
         }
+        if (PASS == PASS_COUNT) {
+            // the neighbours of this pass: its bits that survived the re-decision
+            for (int q = 0; q < nwords; ++q) cnt += __popc(S.bits(lane, q));
+        }
+        __syncwarp();
         constexpr int NROWS = DIM == 3 ? 9 : 3;
         if (cur >= S.rcum[NROWS]) break;
     }
@@ -483,22 +524,26 @@ __device__ __forceinline__ void emit_bits(const TileSmem<C> &S, int lane, int nw
     while (true) {
         int p[EB];
         bool v[EB];
-        next_bits<EB, C, true>(S, lane, 0, cur, p, v);
+        next_bits<EB, C, false, 4>(S, lane, cur, p, v);
         if (!__any_sync(0xffffffffu, v[0])) break;
+        // the valid bits of a call need not be a prefix (a word prefetched at
+        // k = 4 can follow an empty slot): each goes to the next position
+        int o[EB];
+#pragma unroll
+        for (int k = 0; k < EB; ++k) o[k] = (k == 0 ? 0 : o[k - 1] + (v[k - 1] ? 1 : 0));
         if (stg != nullptr) {
 #pragma unroll
             for (int k = 0; k < EB; ++k)
-                if (v[k]) stg[pos + k] = (unsigned short)p[k];
+                if (v[k]) stg[pos + o[k]] = (unsigned short)p[k];
         } else {
             int jv[EB];
 #pragma unroll
             for (int k = 0; k < EB; ++k) jv[k] = jall[v[k] ? p[k] : 0];
 #pragma unroll
             for (int k = 0; k < EB; ++k)
-                if (v[k]) col[pos + k] = jv[k];
+                if (v[k]) col[pos + o[k]] = jv[k];
         }
-#pragma unroll
-        for (int k = 0; k < EB; ++k) pos += v[k] ? 1 : 0;
+        pos += o[EB - 1] + (v[EB - 1] ? 1 : 0);
     }
     __syncwarp();
 }
@@ -739,13 +784,16 @@ __global__ void __launch_bounds__(ROWTILE_NT) k_row_tiles_lb(GridDev g, long lon
     }
 }
 
-// The staged output area (code, pw, f32, then the launch's extra dynamic
-// shared memory) must be one contiguous range.
+// The staged output area (code, pw, the ring, spare, then the launch's extra
+// dynamic shared memory) must be one contiguous range.
 template <class C>
 constexpr bool staging_contiguous() {
-    return offsetof(TileSmem<C>, pw) == offsetof(TileSmem<C>, code) + sizeof(TileSmem<C>::code) &&
-           offsetof(TileSmem<C>, f32) == offsetof(TileSmem<C>, pw) + sizeof(TileSmem<C>::pw) &&
-           sizeof(TileSmem<C>) == offsetof(TileSmem<C>, f32) + sizeof(TileSmem<C>::f32);
+    using SM = TileSmem<C>;
+    return offsetof(SM, pw) == offsetof(SM, code) + sizeof(SM::code) &&
+           offsetof(SM, fxy) == offsetof(SM, pw) + sizeof(SM::pw) &&
+           offsetof(SM, fz) == offsetof(SM, fxy) + sizeof(SM::fxy) &&
+           offsetof(SM, spare) == offsetof(SM, fz) + sizeof(SM::fz) &&
+           sizeof(SM) == offsetof(SM, spare) + sizeof(SM::spare) && sizeof(SM) % 16 == 0;
 }
 static_assert(staging_contiguous<TileSparse>() && staging_contiguous<TileDense>(), "staging layout");
 // the largest launch (every warp with the most extra staging) stays within
