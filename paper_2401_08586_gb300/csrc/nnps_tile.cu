@@ -129,13 +129,12 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// 6 P(R) of Eq. 3 (P without alpha_d) for 0 <= R < 2, without a branch:
-// (2 - R)^3 - 4 max(1 - R, 0)^3 equals (2 - R)^3 on [1, 2) and 4 - 6 R^2 +
-// 3 R^3 = 6 (2/3 - R^2 + R^3 / 2) on [0, 1); the clamp is a saturating add.
-// Only called for neighbours (R < 2); other values are discarded by the
-// caller.  The factor 1/6 is applied once per row.
-__device__ __forceinline__ float w_poly6(float R) {
-    const float t = 2.f - R, s = __saturatef(1.f - R);
+// 6 P(R) of Eq. 3 (P without alpha_d) for R >= 0, without a branch:
+// max(2 - R, 0)^3 - 4 max(1 - R, 0)^3 equals (2 - R)^3 on [1, 2), 4 - 6 R^2 +
+// 3 R^3 = 6 (2/3 - R^2 + R^3 / 2) on [0, 1) and 0 from R = 2 on; the second
+// clamp is a saturating add.  The factor 1/6 is applied once per row.
+__device__ __forceinline__ float w_poly6c(float R) {
+    const float t = fmaxf(2.f - R, 0.f), s = __saturatef(1.f - R);
     return __fmaf_rn(-4.f * s, s * s, t * t * t);
 }
 
@@ -365,10 +364,11 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 
 // The lane's own particle has been removed from its bits by test_window, so
 // every remaining bit is a pair j != i.  The common case (FP32 says
-// "neighbour") runs without branches; a pair the FP32 tier rejects or leaves
-// in its band takes a per-lane branch (FP64 tier out of line; a rejected bit
-// is cleared).  K bits (ring positions p[k], valid v[k]) of the lane's row;
-// q0: first kept word still staged.
+// "neighbour") runs without branches and the density is summed for every
+// valid bit (see below); steps in which some lane holds a pair the FP32 tier
+// rejects or leaves in its band take a warp-uniform branch to decide those
+// (FP64 tier out of line; a rejected bit is cleared).  K bits (ring positions
+// p[k], valid v[k]) of the lane's row; q0: first kept word still staged.
 template <int DIM, int PASS, class C, int K>
 __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int q0,
                                           const int (&p)[K], const bool (&v)[K], int &cnt, float &acc, int *col,
@@ -376,6 +376,7 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
     const int lane = threadIdx.x & 31;
     float r2[K];
     bool in[K];
+    bool odd = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float2 cxy = S.fxy[p[k]];  // p[k] <= RING: invalid bits read the guard slot at worst
@@ -385,7 +386,19 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
         const float d2 = __fsub_rn(cz, h.z32);
         r2[k] = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
         in[k] = v[k] && r2[k] < g.t32_in;
+        odd |= v[k] && !in[k];
     }
+    if (PASS != PASS_EMIT && dens) {
+        // the weight vanishes from R = 2 on, so pairs the FP32 tier rejects
+        // add exactly 0 and band pairs (R within ~1e-6 of 2) less than the
+        // sum's last bit: the density needs no decision
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float wk = w_poly6c(sqrt_approx(r2[k]) * g.r_scale);
+            acc += v[k] ? wk : 0.f;
+        }
+    }
+    if (__any_sync(0xffffffffu, odd))
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (v[k] && !in[k]) {
@@ -403,12 +416,6 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
 #pragma unroll
         for (int k = 0; k < K; ++k)
             if (in[k]) col[rp + cnt++] = S.jall[ring_word<C>(p[k], q0) * 32 + (p[k] & 31)];
-    } else if (dens) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float wk = w_poly6(sqrt_approx(r2[k]) * g.r_scale);
-            acc += in[k] ? wk : 0.f;
-        }
     }
 }
 
