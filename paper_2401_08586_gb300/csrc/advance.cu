@@ -9,6 +9,7 @@
 // once to FP16 / FP32 after each step, exactly as binning rounds them.  The
 // new cells are then put in order by the integer half of binning (histogram,
 // scan, scatter, per-cell sort, gather): no bounds pass, no FP64 conversion.
+#include "cellcount.cuh"
 #include "launch.cuh"
 #include "profile.cuh"
 #include "sph_internal.cuh"
@@ -110,14 +111,10 @@ __global__ void k_advance(GridDev g, const int *__restrict__ scell, const double
             dkey_max = v > dkey_max ? v : dkey_max;
         }
         if (lane == 0 && dkey_max) atomicMax(&g.status->max_key[0], dkey_max);
-        const unsigned int peers = __match_any_sync(0xffffffffu, c);
-        const int leader = __ffs(peers) - 1;
-        int old = 0;
-        if (live && lane == leader) old = atomicAdd(&cnt[c], __popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
+        const int sl = cell_run_slot(c, live, cnt);
         if (live) {
             cid[i] = c;
-            slot[i] = old + __popc(peers & ((1u << lane) - 1u));
+            slot[i] = sl;
         }
     }
 }

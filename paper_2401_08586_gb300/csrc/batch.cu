@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "host.cuh"
+#include "cellcount.cuh"
 #include "launch.cuh"
 #include "profile.cuh"
 #include "sph_internal.cuh"
@@ -102,7 +103,6 @@ __global__ void k_batch_hash(const BinSys *__restrict__ sys, const long long *__
                              long long ntot, int *__restrict__ cnt, int *__restrict__ cid,
                              int *__restrict__ slot, uint2 *__restrict__ rel16u, float4 *__restrict__ rel32u,
                              DevStatus *st) {
-    const int lane = threadIdx.x & 31;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < ntot; base += (long long)gridDim.x * blockDim.x) {
         const long long I = base + threadIdx.x;
         const bool live = I < ntot;
@@ -132,14 +132,10 @@ __global__ void k_batch_hash(const BinSys *__restrict__ sys, const long long *__
             rel16u[I] = q;
             rel32u[I] = f;
         }
-        const unsigned int peers = __match_any_sync(0xffffffffu, c);
-        const int leader = __ffs(peers) - 1;
-        int old = 0;
-        if (live && lane == leader) old = atomicAdd(&cnt[c], __popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
+        const int sl = cell_run_slot(c, live, cnt);
         if (live) {
             cid[I] = c;
-            slot[I] = old + __popc(peers & ((1u << lane) - 1u));
+            slot[I] = sl;
         }
     }
 }

@@ -23,6 +23,7 @@
 // the floor, the difference and its FP32 rounding are exact integer work on
 // the bits of s, since this part's FP64 rate is a small fraction of its
 // FP32 and integer rates.
+#include "cellcount.cuh"
 #include "launch.cuh"
 #include "profile.cuh"
 #include "sortnet.cuh"
@@ -111,7 +112,6 @@ template <int PREC, int DIM>
 __global__ void k_hash(const double *__restrict__ xyz, int n, GridDev g,
                        int *__restrict__ cnt, int *__restrict__ cid, int *__restrict__ slot,
                        uint2 *__restrict__ rel16u, float4 *__restrict__ rel32u, int check_box) {
-    const int lane = threadIdx.x & 31;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
          base += (long long)gridDim.x * blockDim.x) {
         long long i = base + threadIdx.x;
@@ -148,15 +148,10 @@ __global__ void k_hash(const double *__restrict__ xyz, int n, GridDev g,
                 rel32u[i] = f;
             }
         }
-        // Lanes with the same cell add to its counter once.
-        unsigned int peers = __match_any_sync(0xffffffffu, c);
-        int leader = __ffs(peers) - 1;
-        int old = 0;
-        if (live && lane == leader) old = atomicAdd(&cnt[c], __popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
+        const int sl = cell_run_slot(c, live, cnt);
         if (live) {
             cid[i] = c;
-            slot[i] = old + __popc(peers & ((1u << lane) - 1u));
+            slot[i] = sl;
         }
     }
 }
@@ -199,11 +194,14 @@ __device__ __forceinline__ void convert_pos(const GridDev &g, int dim, const Con
 }
 
 constexpr int SORTCV_NT = 128;
-constexpr int SORTCV_SMEM_KEYS = 1024;
+// keys per warp sorted in shared memory: 12 KB per block, so that the 16
+// blocks the SM's threads allow are resident at once and the grid (at most
+// 16 blocks per SM) runs in one wave
+constexpr int SORTCV_SMEM_KEYS = 768;
 
 // Per cell, one warp: sort the cell's input indices (scattered into
 // orig_id in arrival order) ascending -- in registers up to 32, in shared
-// memory up to 1024, longer cells are listed for k_sort_convert_big -- and
+// memory up to 768, longer cells are listed for k_sort_convert_big -- and
 // write every sorted position's outputs.
 template <int PREC>
 __global__ void __launch_bounds__(SORTCV_NT) k_sort_convert(GridDev g, int dim, ConvertOut o, int *__restrict__ keys,
