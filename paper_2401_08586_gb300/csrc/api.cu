@@ -43,10 +43,15 @@ struct sph_grid_s {
     bool rel64_valid = false;
     double drift = 0;       // bound on |rel64 - conversion of xyz| in units of u
     long long own_nnz = 0;
-    DevStatus *h_status = nullptr;  // pinned host mirror
+    DevStatus *h_status = nullptr;  // pinned host mirror, followed by the read-back flag
+    unsigned int status_seq = 0;    // sequence number of the last flagged read-back
     bool async_pending = false;     // sph_search_host_async enqueued, sph_search_host_finish not yet called
     int64_t *async_nnz = nullptr;   // where sph_search_host_finish reports nnz
 };
+
+static unsigned int *status_flag(sph_grid_s *g) {
+    return reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(g->h_status) + sizeof(DevStatus));
+}
 
 static GridDev make_dev(sph_grid_s *g) {
     GridDev d;
@@ -90,6 +95,19 @@ static int read_status(sph_grid_s *g, const long long *rp_nnz = nullptr) {
     return SPH_OK;
 }
 
+// The status record when nothing else the host reads is pending on the
+// stream (binning's bounds): the host spins on a flag the read-back kernel
+// sets after the record, which wakes it sooner than a stream
+// synchronisation; if the flag does not come within 0.2 s (a failed
+// earlier launch, a device that is far behind) the stream is synchronised,
+// which reports any error.
+static int read_status_flagged(sph_grid_s *g) {
+    const unsigned int seq = ++g->status_seq;
+    SPH_CUDA(status_to_host_flag(g->h_status, P<DevStatus>(g->status), status_flag(g), seq, g->stream));
+    if (!wait_host_flag(status_flag(g), seq, 2e5)) SPH_CUDA(cudaStreamSynchronize(g->stream));
+    return SPH_OK;
+}
+
 extern "C" int sph_version(void) { return 100; }
 
 extern "C" int sph_precision_bands(double *tau16, double *tau32) {
@@ -105,7 +123,8 @@ static int grid_create(sph_grid_s **out) {
     if (!g) return fail(SPH_ERR_NOMEM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_status, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_status, sizeof(DevStatus) + 16);
+    if (e == cudaSuccess) *status_flag(g) = 0;
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete g;
@@ -152,7 +171,7 @@ extern "C" int sph_bin_cells(const sph_params *p, const double *xyz, int64_t n, 
                 rc = fail(SPH_ERR_CUDA, "bounds launch failed");
                 break;
             }
-            if ((rc = read_status(g)) != SPH_OK) break;
+            if ((rc = read_status_flagged(g)) != SPH_OK) break;
             if (g->h_status->flags & ST_NONFINITE) {
                 rc = fail(SPH_ERR_INVALID, "non-finite particle coordinate");
                 break;

@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
 #include <string>
 
 #include "host.cuh"
@@ -170,6 +172,15 @@ __global__ void k_status_to_host(DevStatus *host, const DevStatus *st, const lon
     if (threadIdx.x == 0 && nnz_src != nullptr) host->nnz = *nnz_src;
 }
 
+__global__ void k_status_to_host_flag(DevStatus *host, const DevStatus *st, unsigned int *flag, unsigned int seq) {
+    const unsigned int *src = reinterpret_cast<const unsigned int *>(st);
+    unsigned int *dst = reinterpret_cast<unsigned int *>(host);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevStatus) / 4); i += blockDim.x) dst[i] = src[i];
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) *reinterpret_cast<volatile unsigned int *>(flag) = seq;
+}
+
 __global__ void k_gather_i64(long long *host, const long long *src, const long long *idx, int count) {
     for (int i = threadIdx.x; i < count; i += blockDim.x) host[i] = src[idx[i]];
 }
@@ -187,6 +198,27 @@ cudaError_t status_to_host(DevStatus *host_dst, const DevStatus *dev_src, const 
     note_launch(1);
     k_status_to_host<<<1, 32, 0, s>>>(host_dst, dev_src, nnz_src);
     return cudaGetLastError();
+}
+
+cudaError_t status_to_host_flag(DevStatus *host_dst, const DevStatus *dev_src, unsigned int *host_flag,
+                                unsigned int seq, cudaStream_t s) {
+    note_launch(1);
+    k_status_to_host_flag<<<1, 32, 0, s>>>(host_dst, dev_src, host_flag, seq);
+    return cudaGetLastError();
+}
+
+bool wait_host_flag(const unsigned int *host_flag, unsigned int seq, double max_us) {
+    const volatile unsigned int *f = host_flag;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned long long it = 0;; ++it) {
+        if (*f == seq) {
+            std::atomic_thread_fence(std::memory_order_acquire);
+            return true;
+        }
+        if ((it & 1023) == 1023 &&
+            std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count() > max_us)
+            return false;
+    }
 }
 
 cudaError_t gather_i64_to_host(long long *host_dst, const long long *src, const long long *idx, int count,

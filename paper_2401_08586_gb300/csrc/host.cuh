@@ -64,6 +64,14 @@ cudaError_t copy_small_to_host(void *host_dst, const void *dev_src, size_t bytes
 // The status record and, if nnz_src != NULL, the value at nnz_src into the
 // record's nnz field, in one launch.
 cudaError_t status_to_host(DevStatus *host_dst, const DevStatus *dev_src, const long long *nnz_src, cudaStream_t s);
+// The same without nnz, then *host_flag = seq once the record is written and
+// visible to the host (pinned memory), so that the host can wait for it with
+// wait_host_flag instead of synchronising the stream.
+cudaError_t status_to_host_flag(DevStatus *host_dst, const DevStatus *dev_src, unsigned int *host_flag,
+                                unsigned int seq, cudaStream_t s);
+// Spin until *host_flag == seq (then every write the device made before the
+// flag is visible), at most max_us microseconds; false if it timed out.
+bool wait_host_flag(const unsigned int *host_flag, unsigned int seq, double max_us);
 // host_dst[i] = src[idx[i]] for i < count (int64 gathers into pinned memory;
 // idx in pinned host memory too).
 cudaError_t gather_i64_to_host(long long *host_dst, const long long *src, const long long *idx, int count,

@@ -22,7 +22,7 @@ namespace {
 using namespace net;
 
 constexpr int SCAN_NT = 256;
-constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_ITEMS = 4;  // tiles of 1024 items: more blocks in flight for grids of ~10^4-10^5 cells
 constexpr int SCAN_TILE = SCAN_NT * SCAN_ITEMS;
 
 __device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
