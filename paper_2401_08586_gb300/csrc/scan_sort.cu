@@ -229,11 +229,14 @@ __device__ __forceinline__ int ceil_pow2(int x) {
 constexpr int SORT_NT = 128;
 constexpr int WARP_SMEM_KEYS = 1024;
 
+// Segments of up to 128 keys, one warp each, in registers (1, 2 or 4 keys
+// per lane); longer segments are listed in big_list for k_seg_sort_big.  The
+// longer paths live in their own kernel so that their registers do not limit
+// the residency of this one, which sorts nearly all segments.
 template <typename IdxT>
 __global__ void __launch_bounds__(SORT_NT) k_seg_sort_small(int *keys, const IdxT *seg, long long nseg,
                                                              int *big_list, unsigned int *big_count) {
-    __shared__ int wbuf[SORT_NT / 32][WARP_SMEM_KEYS];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     long long gw = ((long long)blockIdx.x * SORT_NT + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * SORT_NT) >> 5;
     for (long long c = gw; c < nseg; c += nw) {
@@ -260,7 +263,29 @@ __global__ void __launch_bounds__(SORT_NT) k_seg_sort_small(int *keys, const Idx
 #pragma unroll
             for (int t = 0; t < 4; ++t)
                 if (t * 32 + lane < len) keys[a + t * 32 + lane] = v[t];
-        } else if (len <= 256) {
+        } else if (lane == 0) {
+            unsigned int slot = atomicAdd(big_count, 1u);
+            big_list[slot] = (int)c;
+        }
+    }
+}
+
+// The listed segments (longer than 128 keys), one warp each: up to 256 keys
+// in registers (8 per lane), up to WARP_SMEM_KEYS in shared memory, longer
+// ones in place in global memory (the same network, the warp's steps ordered
+// by __syncwarp).
+template <typename IdxT>
+__global__ void __launch_bounds__(SORT_NT) k_seg_sort_big(int *keys, const IdxT *seg, const int *big_list,
+                                                           const unsigned int *big_count) {
+    __shared__ int wbuf[SORT_NT / 32][WARP_SMEM_KEYS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long nbig = *big_count;
+    const long long gw = ((long long)blockIdx.x * SORT_NT + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * SORT_NT) >> 5;
+    for (long long bi = gw; bi < nbig; bi += nw) {
+        const long long c = big_list[bi];
+        const long long a = seg[c], len = seg[c + 1] - a;
+        if (len <= 256) {
             int v[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) v[t] = t * 32 + lane < len ? keys[a + t * 32 + lane] : 0x7fffffff;
@@ -270,26 +295,14 @@ __global__ void __launch_bounds__(SORT_NT) k_seg_sort_small(int *keys, const Idx
                 if (t * 32 + lane < len) keys[a + t * 32 + lane] = v[t];
         } else if (len <= WARP_SMEM_KEYS) {
             int *buf = wbuf[w];
-            for (int i = lane; i < len; i += 32) buf[i] = keys[a + i];
+            for (long long i = lane; i < len; i += 32) buf[i] = keys[a + i];
             __syncwarp();
             bitonic_all_ascending(buf, len, lane, 32, WarpSync());
-            for (int i = lane; i < len; i += 32) keys[a + i] = buf[i];
+            for (long long i = lane; i < len; i += 32) keys[a + i] = buf[i];
             __syncwarp();
-        } else if (lane == 0) {
-            unsigned int slot = atomicAdd(big_count, 1u);
-            big_list[slot] = (int)c;
+        } else {
+            bitonic_all_ascending(keys + a, len, lane, 32, WarpSync());
         }
-    }
-}
-
-template <typename IdxT>
-__global__ void __launch_bounds__(SORT_NT) k_seg_sort_big(int *keys, const IdxT *seg, const int *big_list,
-                                                           const unsigned int *big_count) {
-    unsigned int nbig = *big_count;
-    for (unsigned int b = blockIdx.x; b < nbig; b += gridDim.x) {
-        long long c = big_list[b];
-        long long a = seg[c], len = seg[c + 1] - a;
-        bitonic_all_ascending(keys + a, len, threadIdx.x, SORT_NT, BlockSync());
     }
 }
 
@@ -303,7 +316,7 @@ cudaError_t seg_sort_impl(int *keys, const IdxT *seg, long long nseg, int *big_l
     long long blocks = (nseg * 32 + SORT_NT - 1) / SORT_NT;
     if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
     k_seg_sort_small<IdxT><<<(unsigned)blocks, SORT_NT, 0, s>>>(keys, seg, nseg, big_list, big_count);
-    k_seg_sort_big<IdxT><<<(unsigned)sm_count, SORT_NT, 0, s>>>(keys, seg, big_list, big_count);
+    k_seg_sort_big<IdxT><<<(unsigned)sm_count * 4, SORT_NT, 0, s>>>(keys, seg, big_list, big_count);
     return cudaGetLastError();
 }
 
