@@ -252,8 +252,8 @@ inline unsigned long long *cnt_scan_state(int *cnt, long long ncell) {
 }
 
 // Sort every segment [seg_start[c], seg_start[c+1]) of keys ascending, for
-// c < nseg.  Segments longer than 32 are listed in big_list (capacity nseg)
-// with their count in *big_count (device) and sorted by a block-level pass.
+// c < nseg.  Segments longer than 128 are listed in big_list (capacity nseg)
+// with their count in *big_count (device) and sorted by a second pass.
 cudaError_t segmented_sort_i32(int *keys, const int *seg_start, long long nseg, int *big_list,
                                unsigned int *big_count, int sm_count, cudaStream_t s);
 // Same for int64-delimited segments (CSR rows).
