@@ -12,7 +12,13 @@
 //     cell; coordinates are the cell-relative ones of Eq. 6 re-expressed in
 //     the frame of the group's middle cell, X = x_rel + 2 (c_x - x_mid),
 //     Y = y_rel + 2 dy, Z = z_rel + 2 dz (units of u = h_c / 2), so a pair's
-//     difference is the Eq. 7 distance with the scale h_c / 2;
+//     difference is the Eq. 7 distance with the scale h_c / 2; in the dense
+//     shape the FP16 x of a group of an even number of cells is shifted by
+//     one more (-1: frame centre on the face between the middle two cells,
+//     so a two-cell group keeps |X| <= 4 and the narrower FP16 band: fewer
+//     pairs to re-decide where many lie near kh); the FP32 coordinates keep
+//     the cell-centred frame, so distances and densities do not depend on
+//     the shape;
 //   * cull: candidates farther than kh (plus a margin) from the bounding box
 //     of the group's particles cannot be anybody's neighbour and are dropped;
 //     the rest are compacted in candidate order (ascending column);
@@ -70,18 +76,19 @@ constexpr int TILE_MAX_EXTRA_SMEM = 65536;  // largest extra staging a launch ma
 // spare bytes after the last window) holds 2,640 entries, a tile of 32 rows
 // of up to ~80 neighbours.  Dense: 13.7 KB, 16 warps, 832 kept candidates and
 // 3,488 output entries for denser particle sets.
-template <int CMAX_, int WIN_, int NBUF_, int WPB_, int WSM_, int WB_, int SPARE_>
+template <int CMAX_, int WIN_, int NBUF_, int WPB_, int WSM_, int WB_, int SPARE_, bool FACE_>
 struct TileCfg {
     static constexpr int CMAX = CMAX_;
     static constexpr int WIN = WIN_;
-    static constexpr int NBUF = NBUF_;
     static constexpr int RING = NBUF_ * WIN_;  // FP32 slots of the ring
     static constexpr int RW = RING / 32;        // ring words: kept word q is staged at ring word q % RW
-    static constexpr int WW = WIN_ / 32;        // words per window
     static constexpr int WPB = WPB_;
     static constexpr int WSM = WSM_;
     static constexpr int WB = WB_;  // bits in flight per lane in the walk (independent loads and arithmetic)
     static constexpr int SPARE = SPARE_;
+    // FP16 frame centre of an even number of home cells on the face between
+    // the middle two (|X| <= 4 for two-cell groups: the narrower FP16 band)
+    static constexpr bool FACE = FACE_;
     static constexpr int NWORD = CMAX_ / 32;
     // Bitmask matrix: NWORD + 1 words per lane.  With an even row stride the
     // words of lanes l and l + 16 in one column share a bank; lanes 16..31
@@ -93,8 +100,8 @@ struct TileCfg {
     static_assert(NWORD <= 32, "non-empty word masks are 32 bits");
     static_assert(WSM_ % WPB_ == 0, "warps per CTA");
 };
-using TileSparse = TileCfg<672, 128, 2, 2, 20, 4, 480>;
-using TileDense = TileCfg<832, 192, 2, 2, 16, 4, 16>;
+using TileSparse = TileCfg<672, 128, 2, 2, 20, 4, 480, false>;
+using TileDense = TileCfg<832, 192, 2, 2, 16, 4, 16, true>;
 
 
 template <class C>
@@ -112,7 +119,8 @@ struct TileSmem {
     // extra dynamic shared memory of the launch: after the last window they
     // hold the tile's staged output (16-bit kept-candidate slots), stg_slots
     // of them
-    unsigned char code[C::CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5
+    unsigned char code[C::CMAX];  // kept candidates: frame cell offsets (x + 3) | (dy + 1) << 3 | (dz + 1) << 5,
+                                  // and 1 << 7 when the FP16 frame centre is on a cell face (x shift 2 x - 1)
     uint4 pw[C::WIN / 2];         // FP16 pairs of the window under test: word (g*16 + b) = its candidates 32g + b (lo), 32g + 16 + b (hi)
     float2 fxy[C::RING + 2];      // FP32 frame coordinates of the staged windows: kept slot 32 q + b at 32 (q % RW) + b,
     float fz[C::RING + 4];        // then a guard slot (read, never used, by the walk's empty bits)
@@ -159,7 +167,9 @@ struct Home {
 
 // One home group: its cells, frame and candidate rows.
 struct Group {
-    int xa, xb, xm, xlo, xhi;      // home cells [xa, xb], middle xm, candidate cells [xlo, xhi]
+    int xa, xb, xm, xlo, xhi;      // home cells [xa, xb], middle xm, candidate cells [xlo, xhi]; with
+                                   // TileCfg::FACE and an even number of cells the FP16 frame centre is on
+                                   // xm's right face
     float lo[3], hi[3];            // bounding box of the group's particles (frame, FP32)
     unsigned int tau;              // FP16 band (half2 bits)
 };
@@ -224,7 +234,7 @@ __device__ __forceinline__ int cull_fill(TileSmem<C> &S, const GridDev &g, const
             if (keep) {
                 const int pos = kept + __popc(m & ((1u << lane) - 1u));
                 S.jall[pos] = jk[u];
-                S.code[pos] = (unsigned char)((ox + 3) | rt.y);
+                S.code[pos] = (unsigned char)((ox + 3) | rt.y | (C::FACE ? ((G.xa + G.xb) & 1) << 7 : 0));
                 // the tile's own particles are the contiguous range [p0, p0 + nhome)
                 if (jk[u] >= p0 && jk[u] < p0 + nhome) S.selfpos[jk[u] - p0] = (short)pos;
             }
@@ -254,7 +264,8 @@ __device__ __forceinline__ void stage_window(TileSmem<C> &S, const GridDev &g, i
             const float sz = 2.f * (float)((int)((c >> 5) & 3u) - 1);
             const uint2 q16 = g.rel16[j];
             const float4 r32 = g.rel32[j];
-            const __half2 xy = __hadd2(as_h2(q16.x), __floats2half2_rn(sx, sy));
+            // FP16 x shifted one less when the frame centre is on a cell face
+            const __half2 xy = __hadd2(as_h2(q16.x), __floats2half2_rn(C::FACE ? sx - (float)(c >> 7) : sx, sy));
             hx = __low2half(xy);
             hy = __high2half(xy);
             hz = __hadd(__low2half(as_h2(q16.y)), __float2half_rn(sz));
@@ -346,10 +357,13 @@ __device__ __forceinline__ void next_bits(const TileSmem<C> &S, int lane, BitCur
 }
 
 // Kept word of ring position p while windows from word q0 on are staged
-// (the ring holds the RW consecutive kept words from q0).
+// (the ring holds the RW consecutive kept words from q0); r0 = q0 % RW, used
+// when RW is not a power of two (the dense shape).
 template <class C>
-__device__ __forceinline__ int ring_word(int p, int q0) {
-    return q0 + ((p >> 5) - q0 % C::RW + C::RW) % C::RW;
+__device__ __forceinline__ int ring_word(int p, int q0, int r0) {
+    if ((C::RW & (C::RW - 1)) == 0) return q0 + ((p >> 5) - q0 % C::RW + C::RW) % C::RW;
+    const int d = (p >> 5) - r0;
+    return q0 + (d < 0 ? d + C::RW : d);
 }
 
 
@@ -370,7 +384,7 @@ __device__ __noinline__ bool fp64_tier(const GridDev &g, int i, int j) {
 // (FP64 tier out of line; a rejected bit is cleared).  K bits (ring positions
 // p[k], valid v[k]) of the lane's row; q0: first kept word still staged.
 template <int DIM, int PASS, class C, int K>
-__device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int q0,
+__device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, const Home &h, int q0, int r0,
                                           const int (&p)[K], const bool (&v)[K], int &cnt, float &acc, int *col,
                                           long long rp, unsigned int &n32, unsigned int &n64, bool dens) {
     const int lane = threadIdx.x & 31;
@@ -402,7 +416,7 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (v[k] && !in[k]) {
-            const int q = ring_word<C>(p[k], q0);
+            const int q = ring_word<C>(p[k], q0, r0);
             if (r2[k] <= g.t32_out) {
                 ++n64;
                 in[k] = fp64_tier<DIM>(g, h.i, S.jall[q * 32 + (p[k] & 31)]);
@@ -415,7 +429,7 @@ __device__ __forceinline__ void walk_bits(TileSmem<C> &S, const GridDev &g, cons
     if (PASS == PASS_EMIT) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (in[k]) col[rp + cnt++] = S.jall[ring_word<C>(p[k], q0) * 32 + (p[k] & 31)];
+            if (in[k]) col[rp + cnt++] = S.jall[ring_word<C>(p[k], q0, r0) * 32 + (p[k] & 31)];
     }
 }
 
@@ -428,13 +442,14 @@ __device__ __forceinline__ void walk_until(TileSmem<C> &S, const GridDev &g, con
                                            int target, int &taken, int &cnt, float &acc, int *col, long long rp,
                                            unsigned int &n32, unsigned int &n64, bool dens) {
     const int lane = threadIdx.x & 31;
+    const int r0 = (C::RW & (C::RW - 1)) == 0 ? 0 : q0 % C::RW;
     while (__any_sync(0xffffffffu, taken < target)) {
         int p[C::WB];
         bool v[C::WB];
         next_bits<C::WB, C, true>(S, lane, cur, p, v);
 #pragma unroll
         for (int k = 0; k < C::WB; ++k) taken += v[k] ? 1 : 0;
-        walk_bits<DIM, PASS, C, C::WB>(S, g, h, q0, p, v, cnt, acc, col, rp, n32, n64, dens);
+        walk_bits<DIM, PASS, C, C::WB>(S, g, h, q0, r0, p, v, cnt, acc, col, rp, n32, n64, dens);
     }
 }
 
@@ -450,8 +465,9 @@ __device__ __forceinline__ void group_setup(TileSmem<C> &S, const GridDev &g, Ho
     G.xhi = min(G.xb + 1, nx - 1);
     const uint2 q = g.rel16[min(h.i, g.n - 1)];
     const float4 r = g.rel32[min(h.i, g.n - 1)];
+    const int hf = C::FACE ? (G.xa + G.xb) & 1 : 0;
     const float sx = 2.f * (float)(h.x - G.xm);
-    const __half X = __hadd(__low2half(as_h2(q.x)), __float2half_rn(sx));
+    const __half X = __hadd(__low2half(as_h2(q.x)), __float2half_rn(sx - (float)hf));
     h.X = __halves2half2(X, X);
     h.Y = __high2half2(as_h2(q.x));
     h.Z = __low2half2(as_h2(q.y));
@@ -464,8 +480,10 @@ __device__ __forceinline__ void group_setup(TileSmem<C> &S, const GridDev &g, Ho
     G.hi[0] = warp_max(act ? h.x32 : -INFINITY);
     G.hi[1] = warp_max(act ? h.y32 : -INFINITY);
     G.hi[2] = warp_max(act ? h.z32 : -INFINITY);
-    const int mx = 1 + 2 * max(G.xm - G.xlo, G.xhi - G.xm);
-    const __half t = __float2half_rn(mx < 4 ? 0.03f : 0.06f);  // FP16 band for |X| < 4 / < 8
+    // largest FP16 |X| of the group's candidates: 1 + the largest frame shift
+    const int mx = C::FACE ? 1 + max(abs(2 * (G.xlo - G.xm) - hf), abs(2 * (G.xhi - G.xm) - hf))
+                           : 1 + 2 * max(G.xm - G.xlo, G.xhi - G.xm);
+    const __half t = __float2half_rn(mx <= 4 ? 0.03f : 0.06f);  // FP16 band for |X| <= 4 / < 8
     G.tau = h2_bits(__halves2half2(t, t));
     group_rows<DIM, C>(S, g, cy, cz, G);
 }

@@ -163,6 +163,48 @@ def test_fp16_band_sound_in_tile_frame(dim, maxoff, tau):
     assert float((e - (D2 - T))[np.abs(D2 - T) < 0.5].max()) <= (0.0199 if maxoff == 1 else 0.044)
 
 
+def fp16_e_shift(ai, aj, si, sj, T):
+    """Row-tile arithmetic with any integer frame shifts s (X = fl16(q + s)):
+    odd shifts are the frames centred on the face between a two-cell group's
+    cells."""
+    f16 = lambda x: np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+    Xi = f16(f16_of_f32(ai) + si)
+    Xj = f16(f16_of_f32(aj) + sj)
+    d = f16(Xj - Xi)
+    e = f16(d[:, 0] * d[:, 0] - float(t16_up(T)))
+    for k in range(1, ai.shape[1]):
+        e = f16(d[:, k] * d[:, k] + e)
+    return e
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp16_band_sound_in_face_centred_frame(dim):
+    """Two-cell home groups with the FP16 frame centre on the face between
+    their cells: x shifts 2 o - 1 for cell offsets o in -1..2, so |X| <= 4;
+    every true neighbour keeps e below the narrow band, and the rounding
+    stays under the |X| <= 4 bound."""
+    T = 4.0 * (1 - 2.0 ** -29)
+    ai, aj, sh = pairs_near_threshold(1_500_000, dim, T, width=0.1)
+    oi = np.zeros_like(ai)
+    oi[:, 0] = RNG.integers(0, 2, size=ai.shape[0])  # the home in either cell
+    oj = oi + sh
+    ok = (oj[:, 0] >= -1) & (oj[:, 0] <= 2)
+    if dim == 3:
+        ok &= np.all(np.abs(oj[:, 1:]) <= 1, axis=1)
+    ai, aj, oi, oj, sh = ai[ok], aj[ok], oi[ok], oj[ok], sh[ok]
+    si = 2.0 * oi
+    sj = 2.0 * oj
+    si[:, 0] -= 1.0
+    sj[:, 0] -= 1.0
+    assert np.abs(ai[:, 0] + si[:, 0]).max() <= 4 and np.abs(aj[:, 0] + sj[:, 0]).max() <= 4
+    D2 = np.sum((aj + 2.0 * sh - ai) ** 2, axis=1)
+    e = fp16_e_shift(ai, aj, si, sj, T)
+    nb = D2 < T
+    assert nb.sum() > 1000
+    assert np.all(e[nb] < 0.03)
+    assert float((e - (D2 - T))[np.abs(D2 - T) < 0.5].max()) <= 0.0199
+
+
 def test_fp16_band_is_needed():
     """Without the band the FP16 test would lose true neighbours (so the test
     above is not vacuous)."""
