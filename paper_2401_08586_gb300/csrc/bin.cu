@@ -194,9 +194,9 @@ __device__ __forceinline__ void convert_pos(const GridDev &g, int dim, const Con
 }
 
 constexpr int SORTCV_NT = 128;
-// keys per warp sorted in shared memory: 12 KB per block, so that the 16
-// blocks the SM's threads allow are resident at once and the grid (at most
-// 16 blocks per SM) runs in one wave
+// keys per warp sorted in shared memory: 12 KB per block, so that shared
+// memory does not limit the blocks per SM below what the threads and
+// registers allow (the grid is sized to one wave of resident blocks)
 constexpr int SORTCV_SMEM_KEYS = 768;
 
 // Per cell, one warp: sort the cell's input indices (scattered into
@@ -256,6 +256,21 @@ __global__ void __launch_bounds__(SORTCV_NT) k_sort_convert_big(GridDev g, int d
 
 // ---- host launchers ---------------------------------------------------------
 
+// Resident blocks per SM of k_sort_convert<PREC> (its registers, not its
+// shared memory, set the limit), found once per process.
+template <int PREC>
+static int sortcv_per_sm() {
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_convert<PREC>, SORTCV_NT, 0) != cudaSuccess) {
+            (void)cudaGetLastError();  // not a launch error: fall back to the threads' limit
+            b = 2048 / SORTCV_NT;
+        }
+        return b < 1 ? 1 : b;
+    }();
+    return per_sm;
+}
+
 static unsigned grid_for(long long n, int nt, int sm_count, int per_sm) {
     long long b = (n + nt - 1) / nt;
     if (b > (long long)sm_count * per_sm) b = (long long)sm_count * per_sm;
@@ -305,8 +320,12 @@ cudaError_t launch_order_convert(const GridDev &g, int n, int dim, int prec, int
     const bool r = prec == SPH_PREC_FP16_RCLL;
     const ConvertOut o{rank,  scell, scell_x, r ? rel16 : nullptr, r ? rel32 : nullptr, rel16u, rel32u,
                        rel64u, r ? rel64 : nullptr, r ? nullptr : x64};
+    // one wave: the warps loop over the cells, so blocks beyond the resident
+    // ones would only start once others finish and run their cells alone
     long long sb = (g.ncell * 32 + SORTCV_NT - 1) / SORTCV_NT;
-    if (sb > (long long)sm_count * 16) sb = (long long)sm_count * 16;
+    const long long wave =
+        (long long)sm_count * (r ? sortcv_per_sm<SPH_PREC_FP16_RCLL>() : sortcv_per_sm<SPH_PREC_FP64_CLL>());
+    if (sb > wave) sb = wave;
     if (sb < 1) sb = 1;
     if (r) {
         k_sort_convert<SPH_PREC_FP16_RCLL><<<(unsigned)sb, SORTCV_NT, 0, s>>>(g, dim, o, orig_id, cell_start,
