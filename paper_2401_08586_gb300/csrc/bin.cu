@@ -260,14 +260,7 @@ __global__ void __launch_bounds__(SORTCV_NT) k_sort_convert_big(GridDev g, int d
 // shared memory, set the limit), found once per process.
 template <int PREC>
 static int sortcv_per_sm() {
-    static const int per_sm = [] {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_convert<PREC>, SORTCV_NT, 0) != cudaSuccess) {
-            (void)cudaGetLastError();  // not a launch error: fall back to the threads' limit
-            b = 2048 / SORTCV_NT;
-        }
-        return b < 1 ? 1 : b;
-    }();
+    static const int per_sm = resident_blocks((const void *)k_sort_convert<PREC>, SORTCV_NT);
     return per_sm;
 }
 

@@ -8,6 +8,18 @@
 
 namespace sph {
 
+// Blocks of kernel `kern` (nt threads, smem bytes of dynamic shared memory)
+// that one SM holds at once, at least 1 (the per-cell sort of binning runs
+// one wave of these).
+inline int resident_blocks(const void *kern, int nt, size_t smem = 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, nt, smem) != cudaSuccess) {
+        (void)cudaGetLastError();  // a failed query is not a launch error: the threads' limit
+        b = 2048 / nt;
+    }
+    return b < 1 ? 1 : b;
+}
+
 // Binning (bin.cu).
 cudaError_t launch_bounds(const double *xyz, long long n, int dim, DevStatus *st, int sm_count, cudaStream_t s);
 cudaError_t launch_hash_scatter_convert(const GridDev &g, const double *xyz, int n, int dim, int prec, int *cnt,
