@@ -356,10 +356,14 @@ static float time_search(sph_batch_s *b, int dim, long long ntot, long long nrow
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    launch_status_reset_counters(P<DevStatus>(b->status), s);
-    cudaEventRecord(e0, s);
-    cudaError_t err = batch_search(b, dim, ntot, nrow, ntiles_max, out, tv, s);
-    cudaEventRecord(e1, s);
+    // a candidate whose counters could not be reset is not timed (a stale
+    // tile ticket would make its search skip tiles)
+    cudaError_t err = launch_status_reset_counters(P<DevStatus>(b->status), s);
+    if (err == cudaSuccess) {
+        cudaEventRecord(e0, s);
+        err = batch_search(b, dim, ntot, nrow, ntiles_max, out, tv, s);
+        cudaEventRecord(e1, s);
+    }
     float ms = INFINITY;
     if (err == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
     cudaGetLastError();

@@ -312,7 +312,8 @@ cudaError_t seg_sort_impl(int *keys, const IdxT *seg, long long nseg, int *big_l
     if (nseg <= 0) return cudaSuccess;
     ProfScope ps(TAG_SORT, s);
     note_launch(2);
-    cudaMemsetAsync(big_count, 0, sizeof(unsigned int), s);
+    const cudaError_t e = cudaMemsetAsync(big_count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
     long long blocks = (nseg * 32 + SORT_NT - 1) / SORT_NT;
     if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
     k_seg_sort_small<IdxT><<<(unsigned)blocks, SORT_NT, 0, s>>>(keys, seg, nseg, big_list, big_count);
